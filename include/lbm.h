@@ -1,0 +1,169 @@
+/*
+ * C-ABI of the GB300 (sm_103a) direct-coupling multi-level lattice Boltzmann
+ * library: a hierarchy of nested 2:1 refined Cartesian levels advanced with the
+ * H-RR collision (Sec. 2 of Astoul et al., arXiv 2004.14887) and the DC2
+ * direct-coupling cell-vertex interface with recursive sub-cycling (Sec. 3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every call returns LBM_OK (0) or a negative LBM_ERR_* code; the handle's
+ *   lbm_last_error() then holds a one-line message.  Nothing throws across the ABI.
+ * - Arrays are level-local boxes, x fastest: a node (x, y, z) of level l has
+ *   index x + n_x (y + n_y z), with n from lbm_query_level.  Velocity arrays are
+ *   [D][n_nodes].  Values at nodes strictly inside the next finer patch (the
+ *   "hole", class LBM_NODE_HOLE) are ignored on input and written as 0.
+ * - Co-located nodes (a coarse node on the outline of a finer patch and the
+ *   fine node at the same place) must receive identical (rho, u).
+ * - The caller owns every input/output buffer.  With on_device != 0 the
+ *   pointers are device pointers (e.g. torch CUDA tensors) used in order on the
+ *   handle's stream; with on_device == 0 they are host pointers and the call
+ *   synchronises the stream before returning.
+ * - The library owns the population, interface and history arrays.  They are
+ *   allocated at lbm_create_hierarchy through desc->alloc/desc->free when given
+ *   (the Python binding backs them with PyTorch's caching allocator), else
+ *   through cudaMalloc/cudaFree, and released by lbm_destroy.
+ * - All device work is issued on the stream given at creation (a private
+ *   non-blocking stream when NULL) and is stream-ordered.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_MAX_LEVELS 4
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+enum {
+    LBM_OK = 0,
+    LBM_ERR_BAD_DESC = -1,  /* malformed hierarchy description */
+    LBM_ERR_OOM = -2,       /* an allocation failed */
+    LBM_ERR_CUDA = -3,      /* a CUDA runtime call failed */
+    LBM_ERR_NEWTON = -4,    /* Newton at a TF node did not converge in 10 iterations */
+    LBM_ERR_DIVERGED = -5,  /* NaN or Inf met in a reduction */
+    LBM_ERR_TIMEOUT = -6,   /* a bounded device-side wait gave up */
+    LBM_ERR_ARG = -8        /* bad argument (level index, null pointer, size) */
+};
+
+enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2 };  /* population storage precision */
+enum { LBM_NODE_HOLE = 0, LBM_NODE_BULK = 1, LBM_NODE_TF_PARENT = 2, LBM_NODE_HANGING = 3,
+       LBM_NODE_TF_CHILD = 4 };
+
+typedef void *(*lbm_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*lbm_free_fn)(void *ptr, void *ctx);
+
+/*
+ * Hierarchy description.
+ *   lattice     9 (D2Q9, velocities numbered as in the paper's Fig. 1) or 19 (D3Q19,
+ *               the paper's groups: rest, 6 axes, 12 face diagonals).
+ *   n_levels    1..LBM_MAX_LEVELS; level 0 is the coarsest and periodic on every axis.
+ *   coarse_n    level-0 nodes per axis (coarse_n[2] = 1 for D2Q9).
+ *   box_lo/hi   for level l >= 1: the refined patch [lo, hi) in level-0 cell units.
+ *               A patch has (hi-lo)*2^l + 1 nodes per axis (cell-vertex: its outline
+ *               nodes are shared with level l-1), except on an axis it spans
+ *               entirely (lo = 0, hi = coarse_n), where it is periodic.  Each patch
+ *               keeps >= 4 parent cells from its parent's outline and >= 4 parent
+ *               cells per face (Sec. 3 needs a coarse stencil around every TF node
+ *               and four TF nodes along every face for the hanging-node stencil).
+ *   nu0         kinematic viscosity in level-0 lattice units: tau_0 = 1/2 + 3 nu0
+ *               (Eq. linkTauNu), tau_{l+1} = 2 tau_l - 1/2 (Eq. rescTau).
+ *   sigma       H-RR hybridisation weight of Eq. (a12_HRR) (0.98 in the paper).
+ *   dc_variant  2 = DC2 of Table 1 (coarse data on P and M^f); 1 = DC1 (coarse on M^f only).
+ *   storage     LBM_F64 (FP64 storage and arithmetic), LBM_F32 (FP32 storage and
+ *               arithmetic), LBM_F16S (IEEE half storing f_i - w_i, FP32 arithmetic).
+ *               Interface reconstruction (Newton, rescaling, interpolation) is FP64
+ *               in every mode.
+ *   psi_sign    +1/-1 factor on the cubic-Mach correction psi_i of App. A; -1 makes
+ *               the correction cancel the rho u^3 defect with Psi as printed.
+ *   use_graphs  nonzero: lbm_advance replays one captured CUDA graph per coarse step.
+ *   alloc/free/alloc_ctx  optional device allocator (both or neither).
+ */
+typedef struct {
+    int lattice;
+    int n_levels;
+    int64_t coarse_n[3];
+    int64_t box_lo[LBM_MAX_LEVELS][3];
+    int64_t box_hi[LBM_MAX_LEVELS][3];
+    double nu0;
+    double sigma;
+    int dc_variant;
+    int storage;
+    int psi_sign;
+    int use_graphs;
+    lbm_alloc_fn alloc;
+    lbm_free_fn free;
+    void *alloc_ctx;
+} lbm_hierarchy_desc;
+
+typedef struct lbm_hierarchy *lbm_h;
+
+/* Builds levels, node classes, interface tables (Sec. 3.2 sets, Table 1 couples,
+ * App. B corners) and device arrays.  *out is NULL on failure (message via
+ * lbm_create_error()). */
+LBM_API int lbm_create_hierarchy(const lbm_hierarchy_desc *desc, void *cuda_stream, lbm_h *out);
+LBM_API const char *lbm_create_error(void);
+
+/* Box size n[3], box origin (level-l node units) off[3], active node count and tau_l. */
+LBM_API int lbm_query_level(lbm_h h, int level, int64_t n_out[3], int64_t off_out[3], int64_t *n_active,
+                    double *tau_out);
+/* Node class (LBM_NODE_*) of every box node of a level; host buffer of n_x n_y n_z bytes. */
+LBM_API int lbm_node_class(lbm_h h, int level, uint8_t *cls_out);
+
+/* Sets f_i = f_i^(0)(rho, u) (Eq. fEq_herm) on every active node of the level (the
+ * paper's initial state) and resets the step counters; the interface history of
+ * this level is seeded with the same state. rho [n], u [D][n], FP64. */
+LBM_API int lbm_init_fields(lbm_h h, int level, const double *rho, const double *u, int on_device);
+
+/* Advances the whole hierarchy by n coarse steps: level l takes 2^l steps per
+ * coarse step in the order of Sec. 3.5 (asynchronous then synchronous fine
+ * sub-steps, recursively). */
+LBM_API int lbm_advance(lbm_h h, int64_t n_coarse_steps);
+
+/* Density and velocity (zeroth and first moments of the current post-collision
+ * populations) of every box node of a level; hole nodes get 0. rho [n], u [D][n], FP64. */
+LBM_API int lbm_get_macros(lbm_h h, int level, double *rho_out, double *u_out, int on_device);
+/* Current post-collision populations of a level as FP64, [Q][n] (hole nodes 0). */
+LBM_API int lbm_get_pops(lbm_h h, int level, double *f_out, int on_device);
+
+/* FP64 volume-weighted mass and momentum of a level over its active nodes with the
+ * dual-cell weights in level-0 cell volumes (outline nodes weigh the part of their
+ * cell inside the level): out[0] = mass, out[1..3] = momentum.  Returns
+ * LBM_ERR_DIVERGED if a NaN or Inf was met. */
+LBM_API int lbm_reduce(lbm_h h, int level, double out[4]);
+
+/* Device status word accumulated by the kernels since the last call (cleared on read):
+ * returns LBM_OK, LBM_ERR_NEWTON or LBM_ERR_DIVERGED.  Synchronises the stream. */
+LBM_API int lbm_check_status(lbm_h h);
+/* Largest Newton iteration count met since creation. */
+LBM_API int lbm_max_newton_iters(lbm_h h);
+
+/* Kernel timing: while enabled, lbm_advance launches eagerly and brackets every
+ * bulk collide-and-stream launch with CUDA events on the handle's stream.
+ * lbm_timing_read returns, per level, the summed device milliseconds and the
+ * launch count since enabling.  ms_out and launches_out hold n_levels entries. */
+LBM_API int lbm_timing_enable(lbm_h h, int enable);
+LBM_API int lbm_timing_read(lbm_h h, double *ms_out, int64_t *launches_out);
+
+/* Kernel launches issued by lbm_advance so far (every launch counts, graph-replayed or not). */
+LBM_API int64_t lbm_launch_count(lbm_h h);
+
+/* Bytes of device memory held by the handle. */
+LBM_API int64_t lbm_device_bytes(lbm_h h);
+
+LBM_API int lbm_synchronize(lbm_h h);
+LBM_API const char *lbm_last_error(lbm_h h);
+LBM_API void lbm_destroy(lbm_h h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,390 @@
+// Device code of the GB300 direct-coupling multi-level lattice Boltzmann library.
+//
+// Hot path per level sub-step (Sec. 3.5 of Astoul et al., arXiv 2004.14887):
+//   k_hist   coarse post-stream populations at TF nodes and macros on the ring of
+//            coarse stencil nodes -> 3-slot history (for Eq. TempInt)
+//   k_recon  Newton at TF nodes (Eqs. system_fi, updated_macro), fine rebuild of the
+//            gamma=c populations (Eq. rescff) and, on sync sub-steps, coarse rebuild of
+//            every population (Eq. rescfc) -- FP64
+//   k_grad   coarse-stencil S and C = div Psi at TF nodes (Sec. 3.3), x1/2 for the fine
+//            level (Eqs. PijResc, PSIResc) -- FP64
+//   k_ie     4-point 1-D Lagrange of missing populations, S and C at hanging nodes -- FP64
+//   k_bulk   fused pull-stream + moments (tile + 1 halo in shared memory) + centred
+//            finite differences (Eqs. a1FD_scheme, PSI_FD) + H-RR collision
+//            (Eqs. fEq_herm, a12_HRR, a1Proj, a13RR, LBMscheme_reg, App. A) + store
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmg {
+
+enum : int { ST_NEWTON = 1, ST_NAN = 2 };
+enum : signed char { RK_FINE = 0, RK_TF = 1, RK_RING = 2 };
+enum : unsigned char { TILE_FAST = 0, TILE_SKIP = 1, TILE_GENERAL = 2 };
+enum : int { TAG_BULK = -1, TAG_HOLE = -2 };
+
+// ------------------------------------------------------------------ lattices
+template <int Q> struct Lat;
+
+// D2Q9 numbered as the paper's Fig. 1: 0 rest, 1 E, 2 NE, 3 N, 4 NW, 5 W, 6 SW, 7 S, 8 SE
+template <> struct Lat<9> {
+    static constexpr int D = 2, Q = 9;
+    __host__ __device__ static constexpr int c(int i, int a)
+    {
+        return a == 0 ? ((i == 1 || i == 2 || i == 8) ? 1 : ((i == 4 || i == 5 || i == 6) ? -1 : 0))
+                      : (a == 1 ? ((i == 2 || i == 3 || i == 4) ? 1 : ((i == 6 || i == 7 || i == 8) ? -1 : 0)) : 0);
+    }
+    __host__ __device__ static constexpr double w(int i)
+    {
+        return i == 0 ? 4.0 / 9.0 : ((i & 1) ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+};
+
+// D3Q19 in the paper's groups: 0 rest, 1-6 axes, 7-18 face diagonals (opposites adjacent)
+template <> struct Lat<19> {
+    static constexpr int D = 3, Q = 19;
+    __host__ __device__ static constexpr int c(int i, int a)
+    {
+        constexpr int t[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},
+                                  {0, 0, 1},  {0, 0, -1}, {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                                  {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                  {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+        return t[i][a];
+    }
+    __host__ __device__ static constexpr double w(int i)
+    {
+        return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+};
+
+// symmetric tensors: 0 xx, 1 yy, 2 zz, 3 xy, 4 xz, 5 yz
+__host__ __device__ constexpr int sym_index(int a, int b)
+{
+    return a == b ? a : ((a + b == 1) ? 3 : ((a + b == 2) ? 4 : 5));
+}
+
+// ------------------------------------------------------------------ storage
+template <typename S> struct St;
+template <> struct St<double> {
+    using R = double;
+    __device__ static __forceinline__ double ld(const double *p, long long k, double) { return p[k]; }
+    __device__ static __forceinline__ void st(double *p, long long k, double v, double) { p[k] = v; }
+};
+template <> struct St<float> {
+    using R = float;
+    __device__ static __forceinline__ float ld(const float *p, long long k, double) { return p[k]; }
+    __device__ static __forceinline__ void st(float *p, long long k, float v, double) { p[k] = v; }
+};
+// IEEE half storing the deviation f_i - w_i from rest equilibrium, FP32 arithmetic
+template <> struct St<__half> {
+    using R = float;
+    __device__ static __forceinline__ float ld(const __half *p, long long k, double w)
+    {
+        return __half2float(p[k]) + (float)w;
+    }
+    __device__ static __forceinline__ void st(__half *p, long long k, float v, double w)
+    {
+        p[k] = __float2half_rn(v - (float)w);
+    }
+};
+
+// ------------------------------------------------------------------ device views
+struct LevelGeo {
+    int n[3];
+    int per[3];
+    long long N;      // box nodes
+    long long pitch;  // elements between population planes
+};
+
+struct LevelDev {
+    LevelGeo g;
+    void *f[2];              // population buffers (storage type), [Q][pitch]
+    const int *tag;          // per node: TAG_BULK, TAG_HOLE or interface-table index
+    const unsigned char *tile_flag;
+    int tiles[3];
+    double *if_pop;          // interface table: completed post-stream populations [Q][nif]
+    double *if_mac;          // rho, ux, uy, uz [4][nif]
+    double *if_S;            // strain rate [6][nif]
+    double *if_C;            // C_ab = sum_g d_g Psi_abg [6][nif]
+    int nif;
+    double tau;
+};
+
+__device__ __forceinline__ long long node_index(const LevelGeo &g, int x, int y, int z)
+{
+    return (long long)x + (long long)g.n[0] * ((long long)y + (long long)g.n[1] * z);
+}
+
+__device__ __forceinline__ void node_coords(const LevelGeo &g, long long idx, int &x, int &y, int &z)
+{
+    x = (int)(idx % g.n[0]);
+    long long r = idx / g.n[0];
+    y = (int)(r % g.n[1]);
+    z = (int)(r / g.n[1]);
+}
+
+// wrap (periodic) or reject a coordinate; returns false outside a non-periodic box
+__device__ __forceinline__ bool wrap_coord(int &v, int n, int per)
+{
+    if (v < 0) {
+        if (!per) return false;
+        v += n;
+    } else if (v >= n) {
+        if (!per) return false;
+        v -= n;
+    }
+    return true;
+}
+
+// index of node (x,y,z) displaced by (dx,dy,dz), -1 if outside a non-periodic box
+__device__ __forceinline__ long long shifted_index(const LevelGeo &g, long long idx, int dx, int dy, int dz)
+{
+    int x, y, z;
+    node_coords(g, idx, x, y, z);
+    x += dx;
+    y += dy;
+    z += dz;
+    if (!wrap_coord(x, g.n[0], g.per[0]) || !wrap_coord(y, g.n[1], g.per[1]) || !wrap_coord(z, g.n[2], g.per[2]))
+        return -1;
+    return node_index(g, x, y, z);
+}
+
+// ------------------------------------------------------------------ H-RR physics
+// Third-moment deviation Psi_abg of App. A (Eq. Psi), reading: D2Q9 keeps only the
+// aaa components, D3Q19 keeps aaa, aab (= rho u_b u_g^2 / 2) and xyz.
+template <int D, typename R>
+__device__ __forceinline__ void psi_components(R rho, const R *u, R *P)
+{
+    // P: 0 xxx 1 yyy 2 zzz 3 xxy 4 xxz 5 xyy 6 xzz 7 yyz 8 yzz 9 xyz
+    P[0] = rho * u[0] * u[0] * u[0];
+    P[1] = rho * u[1] * u[1] * u[1];
+    if (D == 3) {
+        P[2] = rho * u[2] * u[2] * u[2];
+        P[3] = R(0.5) * rho * u[1] * u[2] * u[2];  // xxy: single y, third z
+        P[4] = R(0.5) * rho * u[2] * u[1] * u[1];  // xxz: single z, third y
+        P[5] = R(0.5) * rho * u[0] * u[2] * u[2];  // xyy: single x, third z
+        P[6] = R(0.5) * rho * u[0] * u[1] * u[1];  // xzz: single x, third y
+        P[7] = R(0.5) * rho * u[2] * u[0] * u[0];  // yyz: single z, third x
+        P[8] = R(0.5) * rho * u[1] * u[0] * u[0];  // yzz: single y, third x
+        P[9] = rho * u[0] * u[1] * u[2];
+    }
+}
+
+// Centred differences from the macros of the 2D axis neighbours (m[b][0] at +e_b,
+// m[b][1] at -e_b), half-width h nodes: S_ab and C_ab = sum_g d_g Psi_abg.
+template <int D, typename R>
+__device__ __forceinline__ void fd_gradients(const R (&rho)[3][2], const R (&u)[3][2][3], R inv2h, R *S, R *C)
+{
+    R du[3][3];  // du[b][a] = d_b u_a
+#pragma unroll
+    for (int b = 0; b < D; b++)
+#pragma unroll
+        for (int a = 0; a < D; a++) du[b][a] = (u[b][0][a] - u[b][1][a]) * inv2h;
+    R dP[3][10];  // dP[g][k] = d_g P_k
+#pragma unroll
+    for (int g = 0; g < D; g++) {
+        R Pp[10], Pm[10];
+        psi_components<D, R>(rho[g][0], u[g][0], Pp);
+        psi_components<D, R>(rho[g][1], u[g][1], Pm);
+#pragma unroll
+        for (int k = 0; k < (D == 3 ? 10 : 2); k++) dP[g][k] = (Pp[k] - Pm[k]) * inv2h;
+    }
+    S[0] = du[0][0];
+    S[1] = du[1][1];
+    S[3] = R(0.5) * (du[1][0] + du[0][1]);
+    if (D == 2) {
+        S[2] = S[4] = S[5] = R(0);
+        C[0] = dP[0][0];
+        C[1] = dP[1][1];
+        C[2] = C[3] = C[4] = C[5] = R(0);
+    } else {
+        S[2] = du[2][2];
+        S[4] = R(0.5) * (du[2][0] + du[0][2]);
+        S[5] = R(0.5) * (du[2][1] + du[1][2]);
+        C[0] = dP[0][0] + dP[1][3] + dP[2][4];  // d_x Pxxx + d_y Pxxy + d_z Pxxz
+        C[1] = dP[0][5] + dP[1][1] + dP[2][7];  // d_x Pxyy + d_y Pyyy + d_z Pyyz
+        C[2] = dP[0][6] + dP[1][8] + dP[2][2];  // d_x Pxzz + d_y Pyzz + d_z Pzzz
+        C[3] = dP[0][3] + dP[1][5] + dP[2][9];  // d_x Pxxy + d_y Pxyy + d_z Pxyz
+        C[4] = dP[0][4] + dP[1][9] + dP[2][6];  // d_x Pxxz + d_y Pxyz + d_z Pxzz
+        C[5] = dP[0][9] + dP[1][7] + dP[2][8];  // d_x Pxyz + d_y Pyyz + d_z Pyzz
+    }
+}
+
+// H-RR collision of one node, Eq. (LBMscheme_reg), in the compact Hermite form
+//   f_i = w_i [ rho (1 + c.u/cs2) + H2_i:B/(2cs2^2) + sum_{a!=b} H3_i,aab T_ab/(2cs2^3) ]
+// with B = rho uu + (1-1/tau) a1 + (s/2) C and T_ab = rho u_a^2 u_b + (1-1/tau) a1_aab,
+// which is f0 + (1-1/tau) f1_reg + psi/2 term by term.  a1 follows Eq. (a12_HRR):
+// a1^PR = sum_i H2_i (f_i - f0_i + psi_i/2) = Pi - cs2 sum(f) I - rho uu + (s/2) C
+// (Hermite orthogonality), a1^FD = -2 tau rho cs2 S.
+template <int Q, typename R>
+__device__ __forceinline__ void hrr_collide(R (&f)[Q], R rho, const R *u, const R *S, const R *C, R tau,
+                                            R sigma, R spsi)
+{
+    using L = Lat<Q>;
+    constexpr int D = L::D;
+    const R cs2 = R(1) / R(3);
+    R Pi[6] = {0, 0, 0, 0, 0, 0};
+    R fsum = R(0);
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        fsum += f[i];
+#pragma unroll
+        for (int a = 0; a < D; a++)
+#pragma unroll
+            for (int b = a; b < D; b++)
+                if (L::c(i, a) * L::c(i, b) != 0) Pi[sym_index(a, b)] += R(L::c(i, a) * L::c(i, b)) * f[i];
+    }
+    const R om = R(1) - R(1) / tau;
+    const R kfd = R(-2) * tau * rho * cs2;
+    R B[6], A[6];
+#pragma unroll
+    for (int a = 0; a < D; a++)
+#pragma unroll
+        for (int b = a; b < D; b++) {
+            const int k = sym_index(a, b);
+            const R ruu = rho * u[a] * u[b];
+            R apr = Pi[k] - ruu + R(0.5) * spsi * C[k];
+            if (a == b) apr -= cs2 * fsum;
+            A[k] = sigma * apr + (R(1) - sigma) * kfd * S[k];
+            B[k] = ruu + om * A[k] + R(0.5) * spsi * C[k];
+        }
+    R T[3][3];
+#pragma unroll
+    for (int a = 0; a < D; a++)
+#pragma unroll
+        for (int b = 0; b < D; b++)
+            if (a != b) T[a][b] = rho * u[a] * u[a] * u[b] + om * (R(2) * u[a] * A[sym_index(a, b)] + u[b] * A[sym_index(a, a)]);
+    R trB = R(0);
+#pragma unroll
+    for (int a = 0; a < D; a++) trB += B[sym_index(a, a)];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        R cu = R(0), h2 = R(0), h3 = R(0);
+#pragma unroll
+        for (int a = 0; a < D; a++)
+            if (L::c(i, a) != 0) cu += R(L::c(i, a)) * u[a];
+#pragma unroll
+        for (int a = 0; a < D; a++) {
+            if (L::c(i, a) != 0) h2 += B[sym_index(a, a)];
+#pragma unroll
+            for (int b = a + 1; b < D; b++)
+                if (L::c(i, a) * L::c(i, b) != 0) h2 += R(2 * L::c(i, a) * L::c(i, b)) * B[sym_index(a, b)];
+        }
+        h2 -= cs2 * trB;
+#pragma unroll
+        for (int a = 0; a < D; a++)
+#pragma unroll
+            for (int b = 0; b < D; b++)
+                if (a != b && L::c(i, b) != 0)
+                    h3 += (R(L::c(i, a) * L::c(i, a)) - cs2) * R(L::c(i, b)) * T[a][b];
+        f[i] = R(L::w(i)) * (rho + R(3) * rho * cu + R(4.5) * h2 + R(13.5) * h3);
+    }
+}
+
+// Equilibrium of Eq. (fEq_herm) and its derivatives with respect to X = (rho, u)
+template <int Q>
+__device__ __forceinline__ double feq_one(int i, double rho, const double *u)
+{
+    using L = Lat<Q>;
+    constexpr int D = L::D;
+    const double cs2 = 1.0 / 3.0;
+    double cu = 0.0, uu = 0.0, h3 = 0.0;
+    for (int a = 0; a < D; a++) {
+        cu += L::c(i, a) * u[a];
+        uu += u[a] * u[a];
+    }
+    for (int a = 0; a < D; a++)
+        for (int b = 0; b < D; b++)
+            if (a != b) h3 += (L::c(i, a) * L::c(i, a) - cs2) * L::c(i, b) * u[a] * u[a] * u[b];
+    return L::w(i) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu + 13.5 * h3);
+}
+
+template <int Q>
+__device__ __forceinline__ void dfeq_one(int i, double rho, const double *u, double feq, double *d)
+{
+    using L = Lat<Q>;
+    constexpr int D = L::D;
+    const double cs2 = 1.0 / 3.0;
+    double cu = 0.0;
+    for (int a = 0; a < D; a++) cu += L::c(i, a) * u[a];
+    d[0] = feq / rho;
+    for (int g = 0; g < D; g++) {
+        double t = 3.0 * L::c(i, g) + 9.0 * cu * L::c(i, g) - 3.0 * u[g];
+        double h = 0.0;
+        for (int b = 0; b < D; b++)
+            if (b != g) h += (L::c(i, g) * L::c(i, g) - cs2) * L::c(i, b) * 2.0 * u[g] * u[b];
+        for (int a = 0; a < D; a++)
+            if (a != g) h += (L::c(i, a) * L::c(i, a) - cs2) * L::c(i, g) * u[a] * u[a];
+        d[1 + g] = L::w(i) * rho * (t + 13.5 * h);
+    }
+}
+
+// Newton-Raphson for F(X) = sum_i Gamma_i Phi_i (fhat_i - f0_i(X)) = 0 (Eq. system_fi),
+// started from the plain moments of fhat, stopped once max|dX| < 1e-12 (Eq. updated_macro).
+template <int Q>
+__device__ int newton_solve(const double *fhat, const double *Gam, double *X)
+{
+    using L = Lat<Q>;
+    constexpr int D = L::D, n = D + 1;
+    double rho = 0.0, m[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < Q; i++) {
+        rho += fhat[i];
+        for (int a = 0; a < D; a++) m[a] += L::c(i, a) * fhat[i];
+    }
+    X[0] = rho;
+    for (int a = 0; a < 3; a++) X[1 + a] = a < D ? m[a] / rho : 0.0;
+    for (int it = 1; it <= 10; it++) {
+        double F[4] = {0, 0, 0, 0}, J[16];
+        for (int k = 0; k < 16; k++) J[k] = 0.0;
+        for (int i = 0; i < Q; i++) {
+            const double fe = feq_one<Q>(i, X[0], X + 1);
+            double d[4];
+            dfeq_one<Q>(i, X[0], X + 1, fe, d);
+            double phi[4] = {1.0, (double)L::c(i, 0), (double)L::c(i, 1), D == 3 ? (double)L::c(i, 2) : 0.0};
+            for (int r = 0; r < n; r++) {
+                F[r] += Gam[i] * phi[r] * (fhat[i] - fe);
+                for (int k = 0; k < n; k++) J[r * n + k] -= Gam[i] * phi[r] * d[k];
+            }
+        }
+        // Gaussian elimination with partial pivoting on J dX = -F
+        double b[4], dX[4];
+        for (int r = 0; r < n; r++) b[r] = -F[r];
+        for (int k = 0; k < n; k++) {
+            int p = k;
+            for (int r = k + 1; r < n; r++)
+                if (fabs(J[r * n + k]) > fabs(J[p * n + k])) p = r;
+            if (J[p * n + k] == 0.0) return -1;
+            if (p != k) {
+                for (int c2 = 0; c2 < n; c2++) {
+                    double t = J[k * n + c2];
+                    J[k * n + c2] = J[p * n + c2];
+                    J[p * n + c2] = t;
+                }
+                double t = b[k];
+                b[k] = b[p];
+                b[p] = t;
+            }
+            for (int r = k + 1; r < n; r++) {
+                double mlt = J[r * n + k] / J[k * n + k];
+                for (int c2 = k; c2 < n; c2++) J[r * n + c2] -= mlt * J[k * n + c2];
+                b[r] -= mlt * b[k];
+            }
+        }
+        for (int k = n - 1; k >= 0; k--) {
+            double s = b[k];
+            for (int c2 = k + 1; c2 < n; c2++) s -= J[k * n + c2] * dX[c2];
+            dX[k] = s / J[k * n + k];
+        }
+        double mx = 0.0;
+        for (int r = 0; r < n; r++) {
+            X[r] += dX[r];
+            mx = fmax(mx, fabs(dX[r]));
+        }
+        if (mx < 1e-12) return it;
+    }
+    return -1;
+}
+
+}  // namespace lbmg

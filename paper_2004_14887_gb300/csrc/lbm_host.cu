@@ -1,0 +1,1038 @@
+// Host side of the GB300 direct-coupling multi-level lattice Boltzmann library:
+// hierarchy geometry, node classification (Sec. 3.2 sets, App. B corners), interface
+// tables, the recursive 2:1 sub-cycling schedule of Sec. 3.5 issued as kernel
+// launches (captured once per coarse-step phase into CUDA graphs), and the C-ABI
+// declared in include/lbm.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_kernels.cuh"
+
+using namespace lbmg;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Level {
+    int64_t n[3] = {1, 1, 1}, off[3] = {0, 0, 0};
+    int per[3] = {1, 1, 1};
+    long long N = 0, pitch = 0;
+    double tau = 0.5;
+    std::vector<uint8_t> cls;
+    std::vector<int> tag;
+    std::vector<unsigned char> tile_flag;
+    int tiles[3] = {1, 1, 1};
+    int nTFP = 0, nIE = 0, nTFC = 0, nif = 0;
+    int64_t n_active = 0;
+    // child-box in this level's node coordinates, for volume weights
+    bool has_child = false;
+    int64_t child_lo[3] = {0, 0, 0}, child_hi[3] = {0, 0, 0};
+    int child_per[3] = {1, 1, 1};
+    // device
+    void *f[2] = {nullptr, nullptr};
+    int *d_tag = nullptr;
+    unsigned char *d_tile = nullptr;
+    double *if_pop = nullptr, *if_mac = nullptr, *if_S = nullptr, *if_C = nullptr;
+    double *d_wnode = nullptr;
+};
+
+struct Iface {  // between coarse level l-1 and fine level l
+    std::vector<long long> tf_fine, tf_coarse, ie_fine, ring_coarse, tf_ridx;
+    std::vector<unsigned int> tf_kf, tf_kc, tf_gc, ie_kf;
+    std::vector<signed char> tf_rkind;
+    std::vector<int> ie_nst, ie_st;
+    std::vector<double> ie_w;
+    IfaceDev dev{};
+    double R = 0.5;
+};
+
+}  // namespace
+
+struct lbm_hierarchy {
+    lbm_hierarchy_desc d{};
+    int Q = 9, D = 2, nl = 1;
+    Level lev[LBM_MAX_LEVELS];
+    Iface ifc[LBM_MAX_LEVELS];  // ifc[l] couples level l-1 and level l (l >= 1)
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<DevBuf> bufs;
+    int64_t device_bytes = 0;
+    int *d_status = nullptr, *d_maxit = nullptr;
+    double *d_partial = nullptr, *d_red = nullptr;
+    int red_blocks = 0;
+    long long ncoarse = 0;  // coarse steps done since init
+    std::map<int, cudaGraphExec_t> graphs;
+    std::map<int, int64_t> graph_launches;
+    int64_t launches = 0;
+    int64_t launch_counter = 0;  // launches issued by the current issue pass
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> ev_pairs;  // (level, event index of the start)
+    double timing_ms[LBM_MAX_LEVELS] = {0, 0, 0, 0};
+    int64_t timing_launches[LBM_MAX_LEVELS] = {0, 0, 0, 0};
+    std::string err;
+};
+
+namespace {
+
+int fail(lbm_h h, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_create_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return fail(h, LBM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+void *dev_alloc(lbm_h h, size_t bytes)
+{
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes == 0) bytes = 256;
+    void *p = nullptr;
+    if (h->d.alloc) p = h->d.alloc(bytes, h->d.alloc_ctx);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    if (p) {
+        h->bufs.push_back({p, bytes});
+        h->device_bytes += (int64_t)bytes;
+    }
+    return p;
+}
+
+// short-lived staging buffers go through the same allocator as the handle's arrays
+void *tmp_alloc(lbm_h h, size_t bytes)
+{
+    void *p = nullptr;
+    if (h->d.alloc) p = h->d.alloc(bytes, h->d.alloc_ctx);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    return p;
+}
+void tmp_free(lbm_h h, void *p)
+{
+    if (!p) return;
+    if (h->d.free) h->d.free(p, h->d.alloc_ctx);
+    else cudaFree(p);
+}
+
+template <typename T>
+T *upload(lbm_h h, const std::vector<T> &v, bool *ok)
+{
+    T *p = (T *)dev_alloc(h, std::max<size_t>(1, v.size()) * sizeof(T));
+    if (!p) {
+        *ok = false;
+        return nullptr;
+    }
+    if (!v.empty() && cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+        *ok = false;
+    return p;
+}
+
+int64_t emod(int64_t a, int64_t n)
+{
+    int64_t r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+int lat_c(int Q, int i, int a) { return Q == 9 ? Lat<9>::c(i, a) : Lat<19>::c(i, a); }
+
+size_t store_size(int storage) { return storage == LBM_F64 ? 8 : (storage == LBM_F32 ? 4 : 2); }
+
+// linear index of global level-l coordinates p, or -1 if not a node of level l
+long long node_of(const lbm_h h, int l, const int64_t *p)
+{
+    const Level &v = h->lev[l];
+    int64_t q[3];
+    for (int a = 0; a < 3; a++) {
+        q[a] = p[a] - v.off[a];
+        if (v.per[a]) q[a] = emod(q[a], v.n[a]);
+        else if (q[a] < 0 || q[a] >= v.n[a]) return -1;
+    }
+    long long idx = q[0] + v.n[0] * (q[1] + v.n[1] * q[2]);
+    if (v.cls[idx] == LBM_NODE_HOLE) return -1;
+    return idx;
+}
+
+void global_of(const Level &v, long long idx, int64_t *p)
+{
+    p[0] = idx % v.n[0] + v.off[0];
+    p[1] = (idx / v.n[0]) % v.n[1] + v.off[1];
+    p[2] = idx / (v.n[0] * v.n[1]) + v.off[2];
+}
+
+// ------------------------------------------------------------------ geometry
+int build_geometry(lbm_h h)
+{
+    const lbm_hierarchy_desc &d = h->d;
+    for (int l = 0; l < h->nl; l++) {
+        Level &v = h->lev[l];
+        for (int a = 0; a < 3; a++) {
+            if (a >= h->D) {
+                v.n[a] = 1;
+                v.off[a] = 0;
+                v.per[a] = 1;
+                continue;
+            }
+            if (l == 0) {
+                v.n[a] = d.coarse_n[a];
+                v.off[a] = 0;
+                v.per[a] = 1;
+                continue;
+            }
+            const int64_t lo = d.box_lo[l][a], hi = d.box_hi[l][a];
+            if (lo == 0 && hi == d.coarse_n[a]) {
+                if (!h->lev[l - 1].per[a]) return fail(nullptr, LBM_ERR_BAD_DESC, "level %d spans axis %d but its parent does not", l, a);
+                v.n[a] = d.coarse_n[a] << l;
+                v.off[a] = 0;
+                v.per[a] = 1;
+                continue;
+            }
+            const int64_t psc = (int64_t)1 << (l - 1);
+            if (hi <= lo) return fail(nullptr, LBM_ERR_BAD_DESC, "level %d: empty patch on axis %d", l, a);
+            if ((hi - lo) * psc < 4) return fail(nullptr, LBM_ERR_BAD_DESC, "level %d: a face needs >= 4 parent cells", l);
+            if (h->lev[l - 1].per[a]) {
+                if (lo * psc < 4 || (d.coarse_n[a] - hi) * psc < 4)
+                    return fail(nullptr, LBM_ERR_BAD_DESC, "level %d: patch within 4 parent cells of the periodic seam", l);
+            } else {
+                const int64_t plo = d.box_lo[l - 1][a], phi = d.box_hi[l - 1][a];
+                if ((lo - plo) * psc < 4 || (phi - hi) * psc < 4)
+                    return fail(nullptr, LBM_ERR_BAD_DESC, "level %d: patch needs 4 parent cells of margin", l);
+            }
+            v.n[a] = ((hi - lo) << l) + 1;
+            v.off[a] = lo << l;
+            v.per[a] = 0;
+        }
+        v.N = (long long)v.n[0] * v.n[1] * v.n[2];
+        v.pitch = (v.N + 31) / 32 * 32;
+        v.tau = l == 0 ? 0.5 + 3.0 * d.nu0 : 2.0 * h->lev[l - 1].tau - 0.5;
+        if (l + 1 < h->nl) {
+            v.has_child = true;
+            for (int a = 0; a < 3; a++) {
+                const int64_t lo = d.box_lo[l + 1][a], hi = d.box_hi[l + 1][a];
+                v.child_per[a] = (a >= h->D) || (lo == 0 && hi == d.coarse_n[a]);
+                v.child_lo[a] = lo << l;
+                v.child_hi[a] = hi << l;
+            }
+        }
+    }
+    // classes
+    for (int l = 0; l < h->nl; l++) {
+        Level &v = h->lev[l];
+        v.cls.assign(v.N, LBM_NODE_BULK);
+        for (long long idx = 0; idx < v.N; idx++) {
+            int64_t p[3];
+            global_of(v, idx, p);
+            uint8_t c = LBM_NODE_BULK;
+            if (v.has_child) {
+                bool closed = true, strict = true;
+                for (int a = 0; a < h->D; a++) {
+                    if (v.child_per[a]) continue;
+                    if (p[a] < v.child_lo[a] || p[a] > v.child_hi[a]) closed = false;
+                    if (p[a] <= v.child_lo[a] || p[a] >= v.child_hi[a]) strict = false;
+                }
+                if (closed) c = strict ? LBM_NODE_HOLE : LBM_NODE_TF_CHILD;
+            }
+            if (l > 0 && c == LBM_NODE_BULK) {
+                bool outline = false, even = true;
+                for (int a = 0; a < h->D; a++) {
+                    const int64_t q = p[a] - v.off[a];
+                    if (!v.per[a] && (q == 0 || q == v.n[a] - 1)) outline = true;
+                    if (emod(p[a], 2) != 0) even = false;
+                }
+                if (outline) c = even ? LBM_NODE_TF_PARENT : LBM_NODE_HANGING;
+            }
+            v.cls[idx] = c;
+        }
+        v.n_active = 0;
+        for (long long idx = 0; idx < v.N; idx++) v.n_active += v.cls[idx] != LBM_NODE_HOLE;
+    }
+    return LBM_OK;
+}
+
+unsigned int full_mask(int Q) { return (Q >= 32) ? 0xffffffffu : ((1u << Q) - 1u); }
+
+// fine-known / coarse-known masks of a node: population i is known on a level if the
+// node x - c_i (x/2 - c_i on the parent) exists there (Sec. 3.2 sets, App. B)
+unsigned int known_mask(const lbm_h h, int l, const int64_t *p)
+{
+    unsigned int m = 0;
+    for (int i = 0; i < h->Q; i++) {
+        int64_t s[3] = {p[0] - lat_c(h->Q, i, 0), p[1] - lat_c(h->Q, i, 1), p[2] - lat_c(h->Q, i, 2)};
+        if (node_of(h, l, s) >= 0) m |= 1u << i;
+    }
+    return m;
+}
+
+int build_interfaces(lbm_h h)
+{
+    const int Q = h->Q, D = h->D;
+    const unsigned int all = full_mask(Q);
+    for (int l = 1; l < h->nl; l++) {
+        Level &F = h->lev[l];
+        Level &C = h->lev[l - 1];
+        Iface &I = h->ifc[l];
+        I.R = 0.5 * F.tau / C.tau;
+        std::vector<int> tf_of(F.N, -1);
+        // TF and hanging nodes of the fine level in index order
+        for (long long idx = 0; idx < F.N; idx++) {
+            int64_t p[3];
+            global_of(F, idx, p);
+            if (F.cls[idx] == LBM_NODE_TF_PARENT) {
+                int64_t pc[3] = {p[0] / 2, p[1] / 2, p[2] / 2};
+                const long long cidx = node_of(h, l - 1, pc);
+                if (cidx < 0 || C.cls[cidx] != LBM_NODE_TF_CHILD)
+                    return fail(nullptr, LBM_ERR_BAD_DESC, "TF node without a co-located coarse node");
+                const unsigned int kf = known_mask(h, l, p), kc = known_mask(h, l - 1, pc);
+                if ((kf | kc) != all) return fail(nullptr, LBM_ERR_BAD_DESC, "TF node misses a population on both levels");
+                tf_of[idx] = (int)I.tf_fine.size();
+                I.tf_fine.push_back(idx);
+                I.tf_coarse.push_back(cidx);
+                I.tf_kf.push_back(kf);
+                I.tf_kc.push_back(kc);
+                // Table 1: DC2 takes coarse data on P and M^f (= every coarse-known
+                // population here), DC1 on M^f only
+                I.tf_gc.push_back(h->d.dc_variant == 1 ? (all & ~kf) : kc);
+            }
+        }
+        for (long long idx = 0; idx < F.N; idx++)
+            if (F.cls[idx] == LBM_NODE_HANGING) {
+                int64_t p[3];
+                global_of(F, idx, p);
+                I.ie_fine.push_back(idx);
+                I.ie_kf.push_back(known_mask(h, l, p));
+            }
+        const int nTF = (int)I.tf_fine.size(), nIE = (int)I.ie_fine.size();
+        // gradient stencil references
+        std::map<long long, int> ring_of;
+        I.tf_rkind.assign((size_t)nTF * 2 * D, RK_FINE);
+        I.tf_ridx.assign((size_t)nTF * 2 * D, 0);
+        for (int t = 0; t < nTF; t++) {
+            int64_t p[3];
+            global_of(F, I.tf_fine[t], p);
+            for (int b = 0; b < D; b++)
+                for (int s = 0; s < 2; s++) {
+                    int64_t y[3] = {p[0], p[1], p[2]};
+                    y[b] += s == 0 ? 2 : -2;
+                    const size_t k = (size_t)t * 2 * D + 2 * b + s;
+                    const long long j = node_of(h, l, y);
+                    if (j >= 0) {
+                        if (F.cls[j] == LBM_NODE_TF_PARENT) {
+                            I.tf_rkind[k] = RK_TF;
+                            I.tf_ridx[k] = tf_of[j];
+                        } else if (F.cls[j] == LBM_NODE_BULK) {
+                            I.tf_rkind[k] = RK_FINE;
+                            I.tf_ridx[k] = j;
+                        } else {
+                            return fail(nullptr, LBM_ERR_BAD_DESC, "TF gradient stencil meets a non-bulk fine node");
+                        }
+                    } else {
+                        int64_t yc[3] = {y[0] / 2, y[1] / 2, y[2] / 2};
+                        const long long jc = node_of(h, l - 1, yc);
+                        if (jc < 0 || C.cls[jc] != LBM_NODE_BULK)
+                            return fail(nullptr, LBM_ERR_BAD_DESC, "TF gradient stencil leaves the coarse bulk");
+                        auto it = ring_of.find(jc);
+                        int r;
+                        if (it == ring_of.end()) {
+                            r = (int)I.ring_coarse.size();
+                            ring_of[jc] = r;
+                            I.ring_coarse.push_back(jc);
+                        } else {
+                            r = it->second;
+                        }
+                        I.tf_rkind[k] = RK_RING;
+                        I.tf_ridx[k] = r;
+                    }
+                }
+        }
+        // hanging-node stencils: per odd axis a 4-point 1-D Lagrange set at the
+        // mid-point (centred -1/16, 9/16, 9/16, -1/16; one-sided 5/16, 15/16, -5/16, 1/16
+        // next to a corner), tensor product over the odd axes
+        I.ie_nst.assign(nIE, 0);
+        I.ie_st.assign((size_t)nIE * 16, 0);
+        I.ie_w.assign((size_t)nIE * 16, 0.0);
+        const double wc[4] = {-1.0 / 16, 9.0 / 16, 9.0 / 16, -1.0 / 16};
+        const double wo[4] = {5.0 / 16, 15.0 / 16, -5.0 / 16, 1.0 / 16};
+        for (int e = 0; e < nIE; e++) {
+            int64_t p[3];
+            global_of(F, I.ie_fine[e], p);
+            int64_t pos[3][4];
+            double wt[3][4];
+            int cnt[3];
+            for (int a = 0; a < 3; a++) {
+                if (a >= D || emod(p[a], 2) == 0) {
+                    cnt[a] = 1;
+                    pos[a][0] = p[a];
+                    wt[a][0] = 1.0;
+                    continue;
+                }
+                cnt[a] = 4;
+                const int64_t q = p[a] - F.off[a];
+                static const int oc[4] = {-3, -1, 1, 3}, olo[4] = {-1, 1, 3, 5}, ohi[4] = {1, -1, -3, -5};
+                const int *o = oc;
+                const double *w = wc;
+                if (!F.per[a] && q - 3 < 0) {
+                    o = olo;
+                    w = wo;
+                } else if (!F.per[a] && q + 3 > F.n[a] - 1) {
+                    o = ohi;
+                    w = wo;
+                }
+                for (int k = 0; k < 4; k++) {
+                    pos[a][k] = p[a] + o[k];
+                    wt[a][k] = w[k];
+                }
+            }
+            int m = 0;
+            for (int i0 = 0; i0 < cnt[0]; i0++)
+                for (int i1 = 0; i1 < cnt[1]; i1++)
+                    for (int i2 = 0; i2 < cnt[2]; i2++) {
+                        int64_t y[3] = {pos[0][i0], pos[1][i1], pos[2][i2]};
+                        const long long j = node_of(h, l, y);
+                        if (j < 0 || F.cls[j] != LBM_NODE_TF_PARENT || m >= 16)
+                            return fail(nullptr, LBM_ERR_BAD_DESC, "hanging-node stencil does not land on TF nodes");
+                        I.ie_st[(size_t)e * 16 + m] = tf_of[j];
+                        I.ie_w[(size_t)e * 16 + m] = wt[0][i0] * wt[1][i1] * wt[2][i2];
+                        m++;
+                    }
+            I.ie_nst[e] = m;
+        }
+        F.nTFP = nTF;
+        F.nIE = nIE;
+        C.nTFC = nTF;
+    }
+    // tables and tags: [TF_PARENT | HANGING | TF_CHILD]
+    for (int l = 0; l < h->nl; l++) {
+        Level &v = h->lev[l];
+        v.nif = v.nTFP + v.nIE + v.nTFC;
+        v.tag.assign(v.N, TAG_BULK);
+        for (long long idx = 0; idx < v.N; idx++)
+            if (v.cls[idx] == LBM_NODE_HOLE) v.tag[idx] = TAG_HOLE;
+        if (l > 0) {
+            const Iface &I = h->ifc[l];
+            for (int t = 0; t < v.nTFP; t++) v.tag[I.tf_fine[t]] = t;
+            for (int e = 0; e < v.nIE; e++) v.tag[I.ie_fine[e]] = v.nTFP + e;
+        }
+        if (l + 1 < h->nl) {
+            const Iface &I = h->ifc[l + 1];
+            const int base = v.nTFP + v.nIE;
+            for (int t = 0; t < (int)I.tf_coarse.size(); t++) v.tag[I.tf_coarse[t]] = base + t;
+        }
+        for (long long idx = 0; idx < v.N; idx++)
+            if (v.tag[idx] == TAG_BULK && v.cls[idx] != LBM_NODE_BULK)
+                return fail(nullptr, LBM_ERR_BAD_DESC, "interface node without a table entry");
+    }
+    return LBM_OK;
+}
+
+constexpr int T2X = 32, T2Y = 8;             // D2Q9 tile
+constexpr int T3X = 32, T3Y = 4, T3Z = 2;    // D3Q19 tile
+
+void build_tiles(lbm_h h)
+{
+    const int TX = h->D == 2 ? T2X : T3X, TY = h->D == 2 ? T2Y : T3Y, TZ = h->D == 2 ? 1 : T3Z;
+    for (int l = 0; l < h->nl; l++) {
+        Level &v = h->lev[l];
+        v.tiles[0] = (int)((v.n[0] + TX - 1) / TX);
+        v.tiles[1] = (int)((v.n[1] + TY - 1) / TY);
+        v.tiles[2] = (int)((v.n[2] + TZ - 1) / TZ);
+        const long long nt = (long long)v.tiles[0] * v.tiles[1] * v.tiles[2];
+        v.tile_flag.assign(nt, TILE_GENERAL);
+        const int rz = h->D == 3 ? 2 : 0;
+        for (long long t = 0; t < nt; t++) {
+            const int bx = (int)(t % v.tiles[0]), by = (int)((t / v.tiles[0]) % v.tiles[1]), bz = (int)(t / ((long long)v.tiles[0] * v.tiles[1]));
+            const int64_t x0 = (int64_t)bx * TX, y0 = (int64_t)by * TY, z0 = (int64_t)bz * TZ;
+            bool any_node = false;
+            for (int64_t z = z0; z < std::min<int64_t>(z0 + TZ, v.n[2]); z++)
+                for (int64_t y = y0; y < std::min<int64_t>(y0 + TY, v.n[1]); y++)
+                    for (int64_t x = x0; x < std::min<int64_t>(x0 + TX, v.n[0]); x++)
+                        if (v.cls[x + v.n[0] * (y + v.n[1] * z)] != LBM_NODE_HOLE) any_node = true;
+            if (!any_node) {
+                v.tile_flag[t] = TILE_SKIP;
+                continue;
+            }
+            bool fast = x0 - 2 >= 0 && x0 + TX + 2 <= v.n[0] && y0 - 2 >= 0 && y0 + TY + 2 <= v.n[1] &&
+                        (h->D == 2 || (z0 - 2 >= 0 && z0 + TZ + 2 <= v.n[2]));
+            for (int64_t z = z0 - rz; fast && z < z0 + TZ + rz; z++)
+                for (int64_t y = y0 - 2; fast && y < y0 + TY + 2; y++)
+                    for (int64_t x = x0 - 2; fast && x < x0 + TX + 2; x++)
+                        if (v.cls[x + v.n[0] * (y + v.n[1] * z)] != LBM_NODE_BULK) fast = false;
+            v.tile_flag[t] = fast ? TILE_FAST : TILE_GENERAL;
+        }
+    }
+}
+
+// dual-cell volume of every node restricted to its level's region, in level-0 cell units
+std::vector<double> node_weights(const lbm_h h, int l)
+{
+    const Level &v = h->lev[l];
+    std::vector<double> w(v.N, 0.0);
+    const double base = std::ldexp(1.0, -h->D * l);
+    for (long long idx = 0; idx < v.N; idx++) {
+        if (v.cls[idx] == LBM_NODE_HOLE) continue;
+        int64_t p[3];
+        global_of(v, idx, p);
+        double own = 1.0, child = v.has_child ? 1.0 : 0.0;
+        for (int a = 0; a < h->D; a++) {
+            const int64_t q = p[a] - v.off[a];
+            if (!v.per[a] && (q == 0 || q == v.n[a] - 1)) own *= 0.5;
+            if (v.has_child && !v.child_per[a]) {
+                if (p[a] < v.child_lo[a] || p[a] > v.child_hi[a]) child = 0.0;
+                else if (p[a] == v.child_lo[a] || p[a] == v.child_hi[a]) child *= 0.5;
+            }
+        }
+        w[idx] = base * (own - child);
+    }
+    return w;
+}
+
+int upload_all(lbm_h h)
+{
+    bool ok = true;
+    const size_t ss = store_size(h->d.storage);
+    const int Q = h->Q;
+    for (int l = 0; l < h->nl; l++) {
+        Level &v = h->lev[l];
+        for (int k = 0; k < 2; k++) {
+            v.f[k] = dev_alloc(h, (size_t)Q * v.pitch * ss);
+            if (!v.f[k]) return fail(h, LBM_ERR_OOM, "population buffer of level %d (%zu bytes)", l, (size_t)Q * v.pitch * ss);
+        }
+        v.d_tag = upload(h, v.tag, &ok);
+        v.d_tile = upload(h, v.tile_flag, &ok);
+        const size_t ni = std::max(1, v.nif);
+        v.if_pop = (double *)dev_alloc(h, ni * Q * sizeof(double));
+        v.if_mac = (double *)dev_alloc(h, ni * 4 * sizeof(double));
+        v.if_S = (double *)dev_alloc(h, ni * 6 * sizeof(double));
+        v.if_C = (double *)dev_alloc(h, ni * 6 * sizeof(double));
+        v.d_wnode = upload(h, node_weights(h, l), &ok);
+        if (!ok || !v.if_pop || !v.if_mac || !v.if_S || !v.if_C) return fail(h, LBM_ERR_OOM, "tables of level %d", l);
+        CK(cudaMemset(v.if_pop, 0, ni * Q * sizeof(double)));
+        CK(cudaMemset(v.if_mac, 0, ni * 4 * sizeof(double)));
+        CK(cudaMemset(v.if_S, 0, ni * 6 * sizeof(double)));
+        CK(cudaMemset(v.if_C, 0, ni * 6 * sizeof(double)));
+    }
+    for (int l = 1; l < h->nl; l++) {
+        Iface &I = h->ifc[l];
+        IfaceDev &g = I.dev;
+        g.nTF = (int)I.tf_fine.size();
+        g.nIE = (int)I.ie_fine.size();
+        g.nRing = (int)I.ring_coarse.size();
+        g.tf_fine = upload(h, I.tf_fine, &ok);
+        g.tf_coarse = upload(h, I.tf_coarse, &ok);
+        g.tf_kf = upload(h, I.tf_kf, &ok);
+        g.tf_kc = upload(h, I.tf_kc, &ok);
+        g.tf_gc = upload(h, I.tf_gc, &ok);
+        g.tf_rkind = upload(h, I.tf_rkind, &ok);
+        g.tf_ridx = upload(h, I.tf_ridx, &ok);
+        g.ie_fine = upload(h, I.ie_fine, &ok);
+        g.ie_kf = upload(h, I.ie_kf, &ok);
+        g.ie_nst = upload(h, I.ie_nst, &ok);
+        g.ie_st = upload(h, I.ie_st, &ok);
+        g.ie_w = upload(h, I.ie_w, &ok);
+        g.ring_coarse = upload(h, I.ring_coarse, &ok);
+        g.hist_f = (double *)dev_alloc(h, (size_t)3 * Q * std::max(1, g.nTF) * sizeof(double));
+        g.hist_m = (double *)dev_alloc(h, (size_t)3 * 4 * std::max(1, g.nRing) * sizeof(double));
+        g.tfc_base = h->lev[l - 1].nTFP + h->lev[l - 1].nIE;
+        g.R = I.R;
+        if (!ok || !g.hist_f || !g.hist_m) return fail(h, LBM_ERR_OOM, "interface %d tables", l);
+    }
+    h->d_status = (int *)dev_alloc(h, 2 * sizeof(int));
+    if (!h->d_status) return fail(h, LBM_ERR_OOM, "status word");
+    h->d_maxit = h->d_status + 1;
+    CK(cudaMemset(h->d_status, 0, 2 * sizeof(int)));
+    h->red_blocks = 304;
+    h->d_partial = (double *)dev_alloc(h, (size_t)h->red_blocks * 4 * sizeof(double) + 4 * sizeof(double));
+    if (!h->d_partial) return fail(h, LBM_ERR_OOM, "reduction scratch");
+    h->d_red = h->d_partial + (size_t)h->red_blocks * 4;
+    return LBM_OK;
+}
+
+LevelDev level_dev(const lbm_h h, int l)
+{
+    const Level &v = h->lev[l];
+    LevelDev d{};
+    for (int a = 0; a < 3; a++) {
+        d.g.n[a] = (int)v.n[a];
+        d.g.per[a] = v.per[a];
+        d.tiles[a] = v.tiles[a];
+    }
+    d.g.N = v.N;
+    d.g.pitch = v.pitch;
+    d.f[0] = v.f[0];
+    d.f[1] = v.f[1];
+    d.tag = v.d_tag;
+    d.tile_flag = v.d_tile;
+    d.if_pop = v.if_pop;
+    d.if_mac = v.if_mac;
+    d.if_S = v.if_S;
+    d.if_C = v.if_C;
+    d.nif = std::max(1, v.nif);
+    d.tau = v.tau;
+    return d;
+}
+
+// ------------------------------------------------------------------ schedule
+template <int Q, typename S>
+struct Sched {
+    static void bulk(lbm_h h, int l, const void *src, void *dst)
+    {
+        const Level &v = h->lev[l];
+        const int nt = v.tiles[0] * v.tiles[1] * v.tiles[2];
+        const double spsi = (double)h->d.psi_sign;
+        int ev = -1;
+        if (h->timing) {
+            ev = (int)h->ev_pairs.size() * 2;
+            while ((int)h->ev_pool.size() < ev + 2) {
+                cudaEvent_t e;
+                cudaEventCreate(&e);
+                h->ev_pool.push_back(e);
+            }
+            cudaEventRecord(h->ev_pool[ev], h->stream);
+        }
+        if constexpr (Lat<Q>::D == 2)
+            k_bulk<Q, S, T2X, T2Y, 1><<<nt, T2X * T2Y, 0, h->stream>>>(level_dev(h, l), (const S *)src, (S *)dst,
+                                                                      h->d.sigma, spsi);
+        else
+            k_bulk<Q, S, T3X, T3Y, T3Z><<<nt, T3X * T3Y * T3Z, 0, h->stream>>>(level_dev(h, l), (const S *)src,
+                                                                              (S *)dst, h->d.sigma, spsi);
+        h->launch_counter++;
+        if (h->timing) {
+            cudaEventRecord(h->ev_pool[ev + 1], h->stream);
+            h->ev_pairs.push_back({l, ev});
+        }
+    }
+
+    static TimeW weights(int phase, long long kp)
+    {
+        TimeW tw{};
+        tw.slot[0] = (int)((kp + 2) % 3);
+        tw.slot[1] = (int)(kp % 3);
+        tw.slot[2] = (int)((kp + 1) % 3);
+        if (phase == 1) {
+            tw.w[0] = 0.0;
+            tw.w[1] = 0.0;
+            tw.w[2] = 1.0;
+        } else if (kp == 0) {
+            tw.w[0] = 0.0;
+            tw.w[1] = 0.5;
+            tw.w[2] = 0.5;
+        } else {
+            tw.w[0] = -1.0 / 8.0;  // Eq. (TempInt)
+            tw.w[1] = 3.0 / 4.0;
+            tw.w[2] = 3.0 / 8.0;
+        }
+        return tw;
+    }
+
+    // one step of level l (Sec. 3.5): k is the level's step index, kp its parent's
+    static void level_step(lbm_h h, int l, long long k, int phase, long long kp)
+    {
+        Level &v = h->lev[l];
+        const void *fA = v.f[k & 1];
+        void *fB = v.f[(k + 1) & 1];
+        const int B = 128;
+        LevelDev dv = level_dev(h, l);
+        if (l + 1 < h->nl) {
+            const IfaceDev &I = h->ifc[l + 1].dev;
+            const int n = I.nTF + I.nRing;
+            if (n > 0) {
+                k_hist<Q, S><<<(n + B - 1) / B, B, 0, h->stream>>>(I, dv.g, (const S *)fA, (int)((k + 1) % 3));
+                h->launch_counter++;
+            }
+        }
+        TimeW tw{};
+        if (l > 0) {
+            tw = weights(phase, kp);
+            const IfaceDev &I = h->ifc[l].dev;
+            if (I.nTF > 0) {
+                k_recon<Q, S><<<(I.nTF + B - 1) / B, B, 0, h->stream>>>(I, dv, level_dev(h, l - 1), (const S *)fA,
+                                                                       tw, phase, h->d_status, h->d_maxit);
+                h->launch_counter++;
+            }
+        }
+        if (l + 1 < h->nl) {
+            level_step(h, l + 1, 2 * k, 0, k);
+            level_step(h, l + 1, 2 * k + 1, 1, k);
+        }
+        if (l > 0) {
+            const IfaceDev &I = h->ifc[l].dev;
+            if (I.nTF > 0) {
+                k_grad<Q, S><<<(I.nTF + B - 1) / B, B, 0, h->stream>>>(I, dv, level_dev(h, l - 1), (const S *)fA, tw,
+                                                                      phase);
+                h->launch_counter++;
+            }
+            if (I.nIE > 0) {
+                k_ie<Q, S><<<(I.nIE + B - 1) / B, B, 0, h->stream>>>(I, dv, (const S *)fA);
+                h->launch_counter++;
+            }
+        }
+        bulk(h, l, fA, fB);
+    }
+
+    static void coarse_step(lbm_h h, long long n) { level_step(h, 0, n, 1, -1); }
+
+    static int init_level(lbm_h h, int l, const double *rho, const double *u)
+    {
+        Level &v = h->lev[l];
+        LevelDev dv = level_dev(h, l);
+        const int B = 256;
+        k_init<Q, S><<<(unsigned)((v.N + B - 1) / B), B, 0, h->stream>>>(dv.g, v.d_tag, rho, u, (S *)v.f[0],
+                                                                           (S *)v.f[1]);
+        if (l + 1 < h->nl) {
+            const IfaceDev &I = h->ifc[l + 1].dev;
+            const int n = I.nTF + I.nRing;
+            if (n > 0) k_hist_seed<Q, S><<<(n + 127) / 128, 128, 0, h->stream>>>(I, dv.g, (const S *)v.f[0]);
+        }
+        return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+    }
+
+    static void macros(lbm_h h, int l, double *rho, double *u, double *pops)
+    {
+        Level &v = h->lev[l];
+        const long long k = h->ncoarse << l;
+        LevelDev dv = level_dev(h, l);
+        const int B = 256;
+        k_macros<Q, S><<<(unsigned)((v.N + B - 1) / B), B, 0, h->stream>>>(dv.g, v.d_tag, (const S *)v.f[k & 1],
+                                                                             rho, u, pops);
+    }
+
+    static void reduce(lbm_h h, int l)
+    {
+        Level &v = h->lev[l];
+        const long long k = h->ncoarse << l;
+        LevelDev dv = level_dev(h, l);
+        k_reduce_partial<Q, S><<<h->red_blocks, 256, 0, h->stream>>>(dv.g, v.d_tag, (const S *)v.f[k & 1], v.d_wnode,
+                                                                      h->d_partial, h->d_status);
+        k_reduce_final<<<1, 256, 0, h->stream>>>(h->d_partial, h->red_blocks, h->d_red);
+    }
+};
+
+template <typename Fn>
+void dispatch(lbm_h h, Fn &&fn)
+{
+    if (h->Q == 9) {
+        if (h->d.storage == LBM_F64) fn(Sched<9, double>());
+        else if (h->d.storage == LBM_F32) fn(Sched<9, float>());
+        else fn(Sched<9, __half>());
+    } else {
+        if (h->d.storage == LBM_F64) fn(Sched<19, double>());
+        else if (h->d.storage == LBM_F32) fn(Sched<19, float>());
+        else fn(Sched<19, __half>());
+    }
+}
+
+int issue_coarse_step(lbm_h h, long long n)
+{
+    h->launch_counter = 0;
+    dispatch(h, [&](auto s) { decltype(s)::coarse_step(h, n); });
+    h->launches += h->launch_counter;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(h, LBM_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+int run_graph(lbm_h h, long long n)
+{
+    const int key = (int)(n % 6);
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        h->launch_counter = 0;
+        dispatch(h, [&](auto s) { decltype(s)::coarse_step(h, n); });
+        const int64_t cnt = h->launch_counter;
+        CK(cudaStreamEndCapture(h->stream, &g));
+        cudaGraphExec_t ge;
+        CK(cudaGraphInstantiate(&ge, g, 0));
+        cudaGraphDestroy(g);
+        it = h->graphs.emplace(key, ge).first;
+        h->graph_launches[key] = cnt;
+    }
+    CK(cudaGraphLaunch(it->second, h->stream));
+    h->launches += h->graph_launches[key];
+    return LBM_OK;
+}
+
+bool check_level(lbm_h h, int level)
+{
+    if (!h) return false;
+    if (level < 0 || level >= h->nl) {
+        fail(h, LBM_ERR_ARG, "level %d out of range [0,%d)", level, h->nl);
+        return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+// ================================================================== C-ABI
+extern "C" {
+
+const char *lbm_create_error(void) { return g_create_error.c_str(); }
+
+int lbm_create_hierarchy(const lbm_hierarchy_desc *desc, void *cuda_stream, lbm_h *out)
+{
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!desc) return fail(nullptr, LBM_ERR_ARG, "desc is NULL");
+    if (desc->lattice != 9 && desc->lattice != 19) return fail(nullptr, LBM_ERR_BAD_DESC, "lattice must be 9 or 19");
+    if (desc->n_levels < 1 || desc->n_levels > LBM_MAX_LEVELS) return fail(nullptr, LBM_ERR_BAD_DESC, "n_levels out of range");
+    if (desc->storage < LBM_F64 || desc->storage > LBM_F16S) return fail(nullptr, LBM_ERR_BAD_DESC, "bad storage");
+    if (desc->dc_variant != 1 && desc->dc_variant != 2) return fail(nullptr, LBM_ERR_BAD_DESC, "dc_variant must be 1 or 2");
+    if (!(desc->nu0 > 0.0) || !(desc->sigma >= 0.0 && desc->sigma <= 1.0))
+        return fail(nullptr, LBM_ERR_BAD_DESC, "nu0 must be > 0 and sigma in [0,1]");
+    if ((desc->alloc == nullptr) != (desc->free == nullptr)) return fail(nullptr, LBM_ERR_BAD_DESC, "alloc and free go together");
+    const int D = desc->lattice == 9 ? 2 : 3;
+    for (int a = 0; a < 3; a++) {
+        if (desc->coarse_n[a] < 1 || desc->coarse_n[a] > (1 << 20)) return fail(nullptr, LBM_ERR_BAD_DESC, "coarse_n out of range");
+        if (a >= D && desc->coarse_n[a] != 1) return fail(nullptr, LBM_ERR_BAD_DESC, "coarse_n[2] must be 1 for D2Q9");
+        if (a < D && desc->coarse_n[a] < 8) return fail(nullptr, LBM_ERR_BAD_DESC, "coarse_n must be >= 8");
+    }
+    lbm_h h = new lbm_hierarchy();
+    h->d = *desc;
+    h->Q = desc->lattice;
+    h->D = D;
+    h->nl = desc->n_levels;
+    int rc = build_geometry(h);
+    if (rc == LBM_OK) rc = build_interfaces(h);
+    if (rc != LBM_OK) {
+        delete h;
+        return rc;
+    }
+    build_tiles(h);
+    for (int l = 0; l < h->nl; l++)
+        if (h->lev[l].N > (long long)2147483647) {
+            delete h;
+            return fail(nullptr, LBM_ERR_BAD_DESC, "level %d has more than 2^31 box nodes", l);
+        }
+    if (cuda_stream) {
+        h->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete h;
+            return fail(nullptr, LBM_ERR_CUDA, "cudaStreamCreateWithFlags failed");
+        }
+        h->own_stream = true;
+    }
+    rc = upload_all(h);
+    if (rc != LBM_OK) {
+        g_create_error = h->err;
+        lbm_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_query_level(lbm_h h, int level, int64_t n_out[3], int64_t off_out[3], int64_t *n_active, double *tau_out)
+{
+    if (!check_level(h, level)) return h ? LBM_ERR_ARG : LBM_ERR_ARG;
+    const Level &v = h->lev[level];
+    for (int a = 0; a < 3; a++) {
+        if (n_out) n_out[a] = v.n[a];
+        if (off_out) off_out[a] = v.off[a];
+    }
+    if (n_active) *n_active = v.n_active;
+    if (tau_out) *tau_out = v.tau;
+    return LBM_OK;
+}
+
+int lbm_node_class(lbm_h h, int level, uint8_t *cls_out)
+{
+    if (!check_level(h, level)) return LBM_ERR_ARG;
+    if (!cls_out) return fail(h, LBM_ERR_ARG, "cls_out is NULL");
+    memcpy(cls_out, h->lev[level].cls.data(), h->lev[level].N);
+    return LBM_OK;
+}
+
+int lbm_init_fields(lbm_h h, int level, const double *rho, const double *u, int on_device)
+{
+    if (!check_level(h, level)) return LBM_ERR_ARG;
+    if (!rho || !u) return fail(h, LBM_ERR_ARG, "rho/u is NULL");
+    const Level &v = h->lev[level];
+    const double *drho = rho, *du = u;
+    double *tmp = nullptr;
+    if (!on_device) {
+        tmp = (double *)tmp_alloc(h, (size_t)(1 + h->D) * v.N * sizeof(double));
+        if (!tmp) return fail(h, LBM_ERR_OOM, "staging buffer");
+        CK(cudaMemcpyAsync(tmp, rho, v.N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(tmp + v.N, u, (size_t)h->D * v.N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        drho = tmp;
+        du = tmp + v.N;
+    }
+    int rc = LBM_OK;
+    dispatch(h, [&](auto s) { rc = decltype(s)::init_level(h, level, drho, du); });
+    h->ncoarse = 0;
+    if (tmp) {
+        CK(cudaStreamSynchronize(h->stream));
+        tmp_free(h, tmp);
+    }
+    if (rc != LBM_OK) return fail(h, rc, "init kernel launch failed");
+    return LBM_OK;
+}
+
+int lbm_advance(lbm_h h, int64_t n)
+{
+    if (!h) return LBM_ERR_ARG;
+    if (n < 0) return fail(h, LBM_ERR_ARG, "negative step count");
+    for (int64_t s = 0; s < n; s++) {
+        const long long k = h->ncoarse;
+        int rc;
+        if (h->d.use_graphs && !h->timing && k >= 1) rc = run_graph(h, k);
+        else rc = issue_coarse_step(h, k);
+        if (rc != LBM_OK) return rc;
+        h->ncoarse++;
+    }
+    return LBM_OK;
+}
+
+static int get_common(lbm_h h, int level, double *rho, double *u, double *pops, int on_device)
+{
+    const Level &v = h->lev[level];
+    if (on_device) {
+        dispatch(h, [&](auto s) { decltype(s)::macros(h, level, rho, u, pops); });
+        CK(cudaGetLastError());
+        return LBM_OK;
+    }
+    const size_t nr = rho ? v.N : 0, nu = u ? (size_t)h->D * v.N : 0, np = pops ? (size_t)h->Q * v.N : 0;
+    double *tmp = (double *)tmp_alloc(h, (nr + nu + np + 1) * sizeof(double));
+    if (!tmp) return fail(h, LBM_ERR_OOM, "staging buffer");
+    double *dr = rho ? tmp : nullptr, *dd = u ? tmp + nr : nullptr, *dp = pops ? tmp + nr + nu : nullptr;
+    dispatch(h, [&](auto s) { decltype(s)::macros(h, level, dr, dd, dp); });
+    CK(cudaGetLastError());
+    if (rho) CK(cudaMemcpyAsync(rho, dr, nr * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (u) CK(cudaMemcpyAsync(u, dd, nu * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (pops) CK(cudaMemcpyAsync(pops, dp, np * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    tmp_free(h, tmp);
+    return LBM_OK;
+}
+
+int lbm_get_macros(lbm_h h, int level, double *rho_out, double *u_out, int on_device)
+{
+    if (!check_level(h, level)) return LBM_ERR_ARG;
+    if (!rho_out && !u_out) return fail(h, LBM_ERR_ARG, "no output");
+    return get_common(h, level, rho_out, u_out, nullptr, on_device);
+}
+
+int lbm_get_pops(lbm_h h, int level, double *f_out, int on_device)
+{
+    if (!check_level(h, level)) return LBM_ERR_ARG;
+    if (!f_out) return fail(h, LBM_ERR_ARG, "f_out is NULL");
+    return get_common(h, level, nullptr, nullptr, f_out, on_device);
+}
+
+int lbm_reduce(lbm_h h, int level, double out[4])
+{
+    if (!check_level(h, level)) return LBM_ERR_ARG;
+    if (!out) return fail(h, LBM_ERR_ARG, "out is NULL");
+    dispatch(h, [&](auto s) { decltype(s)::reduce(h, level); });
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, h->d_red, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    int st = 0;
+    CK(cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & ST_NAN) return fail(h, LBM_ERR_DIVERGED, "NaN or Inf in level %d", level);
+    return LBM_OK;
+}
+
+int lbm_check_status(lbm_h h)
+{
+    if (!h) return LBM_ERR_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    int st = 0;
+    CK(cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(h->d_status, 0, sizeof(int)));
+    if (st & ST_NEWTON) return fail(h, LBM_ERR_NEWTON, "Newton did not converge at a TF node");
+    if (st & ST_NAN) return fail(h, LBM_ERR_DIVERGED, "NaN or Inf met");
+    return LBM_OK;
+}
+
+int lbm_max_newton_iters(lbm_h h)
+{
+    if (!h) return LBM_ERR_ARG;
+    int v = 0;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ERR_CUDA;
+    if (cudaMemcpy(&v, h->d_maxit, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LBM_ERR_CUDA;
+    return v;
+}
+
+int lbm_timing_enable(lbm_h h, int enable)
+{
+    if (!h) return LBM_ERR_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    h->timing = enable != 0;
+    h->ev_pairs.clear();
+    for (int l = 0; l < LBM_MAX_LEVELS; l++) {
+        h->timing_ms[l] = 0.0;
+        h->timing_launches[l] = 0;
+    }
+    return LBM_OK;
+}
+
+int lbm_timing_read(lbm_h h, double *ms_out, int64_t *launches_out)
+{
+    if (!h) return LBM_ERR_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    for (auto &pr : h->ev_pairs) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, h->ev_pool[pr.second], h->ev_pool[pr.second + 1]));
+        h->timing_ms[pr.first] += ms;
+        h->timing_launches[pr.first]++;
+    }
+    h->ev_pairs.clear();
+    for (int l = 0; l < h->nl; l++) {
+        if (ms_out) ms_out[l] = h->timing_ms[l];
+        if (launches_out) launches_out[l] = h->timing_launches[l];
+    }
+    return LBM_OK;
+}
+
+int64_t lbm_launch_count(lbm_h h) { return h ? h->launches : 0; }
+int64_t lbm_device_bytes(lbm_h h) { return h ? h->device_bytes : 0; }
+
+int lbm_synchronize(lbm_h h)
+{
+    if (!h) return LBM_ERR_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+const char *lbm_last_error(lbm_h h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void lbm_destroy(lbm_h h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
+    for (auto &b : h->bufs) {
+        if (h->d.free) h->d.free(b.p, h->d.alloc_ctx);
+        else cudaFree(b.p);
+    }
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,266 @@
+"""Thin ctypes binding of the C-ABI in ``include/lbm.h`` (same names, argument
+marshalling only).  Every step of the method runs in the CUDA library
+``_lib/liblbm_gb300.so``; there is no Python or CPU fallback: if the library
+or a CUDA device is missing, the calls raise.
+
+PyTorch supplies device memory (the library's arrays come from PyTorch's
+caching allocator through the allocator callbacks of the description) and the
+stream (the current torch stream of the device at creation).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "liblbm_gb300.so")
+MAX_LEVELS = 4
+
+LBM_OK, LBM_ERR_BAD_DESC, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_NEWTON, LBM_ERR_DIVERGED, LBM_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
+LBM_ERR_ARG = -8
+STORAGE = {"f64": 0, "f32": 1, "f16s": 2}
+HOLE, BULK, TF_PARENT, HANGING, TF_CHILD = 0, 1, 2, 3, 4
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class lbm_hierarchy_desc(C.Structure):
+    _fields_ = [
+        ("lattice", C.c_int),
+        ("n_levels", C.c_int),
+        ("coarse_n", C.c_int64 * 3),
+        ("box_lo", (C.c_int64 * 3) * MAX_LEVELS),
+        ("box_hi", (C.c_int64 * 3) * MAX_LEVELS),
+        ("nu0", C.c_double),
+        ("sigma", C.c_double),
+        ("dc_variant", C.c_int),
+        ("storage", C.c_int),
+        ("psi_sign", C.c_int),
+        ("use_graphs", C.c_int),
+        ("alloc", ALLOC_FN),
+        ("free", FREE_FN),
+        ("alloc_ctx", C.c_void_p),
+    ]
+
+
+EXPORTS = [
+    "lbm_create_hierarchy", "lbm_create_error", "lbm_query_level", "lbm_node_class", "lbm_init_fields",
+    "lbm_advance", "lbm_get_macros", "lbm_get_pops", "lbm_reduce", "lbm_check_status", "lbm_max_newton_iters",
+    "lbm_timing_enable", "lbm_timing_read", "lbm_launch_count", "lbm_device_bytes", "lbm_synchronize",
+    "lbm_last_error", "lbm_destroy",
+]
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                           "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+    L = C.CDLL(LIB_PATH)
+    vp, i64p, dp = C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)
+    L.lbm_create_hierarchy.argtypes = [C.POINTER(lbm_hierarchy_desc), vp, C.POINTER(vp)]
+    L.lbm_create_error.restype = C.c_char_p
+    L.lbm_query_level.argtypes = [vp, C.c_int, i64p, i64p, i64p, dp]
+    L.lbm_node_class.argtypes = [vp, C.c_int, vp]
+    L.lbm_init_fields.argtypes = [vp, C.c_int, vp, vp, C.c_int]
+    L.lbm_advance.argtypes = [vp, C.c_int64]
+    L.lbm_get_macros.argtypes = [vp, C.c_int, vp, vp, C.c_int]
+    L.lbm_get_pops.argtypes = [vp, C.c_int, vp, C.c_int]
+    L.lbm_reduce.argtypes = [vp, C.c_int, dp]
+    L.lbm_check_status.argtypes = [vp]
+    L.lbm_max_newton_iters.argtypes = [vp]
+    L.lbm_timing_enable.argtypes = [vp, C.c_int]
+    L.lbm_timing_read.argtypes = [vp, dp, i64p]
+    L.lbm_launch_count.argtypes = [vp]
+    L.lbm_launch_count.restype = C.c_int64
+    L.lbm_device_bytes.argtypes = [vp]
+    L.lbm_device_bytes.restype = C.c_int64
+    L.lbm_synchronize.argtypes = [vp]
+    L.lbm_last_error.argtypes = [vp]
+    L.lbm_last_error.restype = C.c_char_p
+    L.lbm_destroy.argtypes = [vp]
+    L.lbm_destroy.restype = None
+    _lib = L
+    return L
+
+
+def make_desc(desc: dict, use_graphs: bool = True) -> lbm_hierarchy_desc:
+    d = lbm_hierarchy_desc()
+    d.lattice = int(desc["lattice"])
+    boxes = desc.get("boxes", [])
+    d.n_levels = 1 + len(boxes)
+    cn = list(desc["coarse_n"]) + [1] * (3 - len(desc["coarse_n"]))
+    for a in range(3):
+        d.coarse_n[a] = int(cn[a])
+    for l, (lo, hi) in enumerate(boxes, start=1):
+        for a in range(3):
+            d.box_lo[l][a] = int(lo[a]) if a < len(lo) else 0
+            d.box_hi[l][a] = int(hi[a]) if a < len(hi) else 1
+    d.nu0 = float(desc["nu0"])
+    d.sigma = float(desc.get("sigma", 0.98))
+    d.dc_variant = int(desc.get("dc_variant", 2))
+    d.storage = STORAGE[desc.get("storage", "f64")]
+    d.psi_sign = int(desc.get("psi_sign", -1))
+    d.use_graphs = int(bool(use_graphs))
+    return d
+
+
+class _TorchAllocator:
+    """Device allocator callbacks backed by PyTorch's caching allocator."""
+
+    def __init__(self, torch, device, stream):
+        self._torch, self._dev, self._stream = torch, device, stream
+
+        def _alloc(nbytes, _ctx):
+            try:
+                return int(self._torch.cuda.caching_allocator_alloc(int(nbytes), self._dev, self._stream))
+            except Exception:  # out of memory: the library turns NULL into LBM_ERR_OOM
+                return None
+
+        def _free(ptr, _ctx):
+            if ptr:
+                self._torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.free = FREE_FN(_free)
+
+
+def _ptr(a):
+    """Device pointer of a torch tensor or host pointer of a numpy array, plus on_device flag."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(C.c_void_p), 0
+    return C.c_void_p(a.data_ptr()), 1
+
+
+class Hierarchy:
+    """Handle of one hierarchy on the current CUDA device (see include/lbm.h)."""
+
+    def __init__(self, desc: dict, use_graphs: bool = True, torch_alloc: bool = True, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required: the library has no CPU path")
+        L = lib()
+        self.torch = torch
+        self.device = torch.cuda.current_device()
+        self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
+        d = make_desc(desc, use_graphs)
+        self._alloc = None
+        if torch_alloc:
+            self._alloc = _TorchAllocator(torch, self.device, self._stream_obj.cuda_stream)
+            d.alloc, d.free = self._alloc.alloc, self._alloc.free
+        self._desc = d
+        h = C.c_void_p()
+        rc = L.lbm_create_hierarchy(C.byref(d), C.c_void_p(self._stream_obj.cuda_stream), C.byref(h))
+        if rc != LBM_OK:
+            raise LbmError(rc, L.lbm_create_error().decode())
+        self._h = h
+        self.q = d.lattice
+        self.D = 2 if self.q == 9 else 3
+        self.n_levels = d.n_levels
+        self.levels = [self.query_level(l) for l in range(self.n_levels)]
+
+    # -------------------------------------------------------------- helpers
+    def _check(self, rc):
+        if rc != LBM_OK:
+            raise LbmError(rc, lib().lbm_last_error(self._h).decode())
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().lbm_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -------------------------------------------------------------- C-ABI
+    def query_level(self, l):
+        n = (C.c_int64 * 3)()
+        off = (C.c_int64 * 3)()
+        na = C.c_int64()
+        tau = C.c_double()
+        self._check(lib().lbm_query_level(self._h, l, n, off, C.byref(na), C.byref(tau)))
+        return {"n": tuple(n), "off": tuple(off), "n_active": na.value, "tau": tau.value, "N": n[0] * n[1] * n[2]}
+
+    def node_class(self, l):
+        out = np.zeros(self.levels[l]["N"], dtype=np.uint8)
+        self._check(lib().lbm_node_class(self._h, l, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def init_fields(self, l, rho, u):
+        """rho [N], u [D, N] as float64 numpy arrays (host) or CUDA tensors (device)."""
+        N = self.levels[l]["N"]
+        if isinstance(rho, np.ndarray):
+            rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(N)
+            u = np.ascontiguousarray(u, dtype=np.float64).reshape(self.D, N)
+        pr, dev = _ptr(rho)
+        pu, _ = _ptr(u)
+        self._check(lib().lbm_init_fields(self._h, l, pr, pu, dev))
+
+    def advance(self, n):
+        self._check(lib().lbm_advance(self._h, int(n)))
+
+    def get_macros(self, l, out=None):
+        """(rho [N], u [D, N]) as numpy (out=None) or into the given CUDA tensors."""
+        N = self.levels[l]["N"]
+        if out is None:
+            rho = np.zeros(N)
+            u = np.zeros((self.D, N))
+        else:
+            rho, u = out
+        pr, dev = _ptr(rho)
+        pu, _ = _ptr(u)
+        self._check(lib().lbm_get_macros(self._h, l, pr, pu, dev))
+        return rho, u
+
+    def get_pops(self, l):
+        f = np.zeros((self.q, self.levels[l]["N"]))
+        self._check(lib().lbm_get_pops(self._h, l, f.ctypes.data_as(C.c_void_p), 0))
+        return f
+
+    def reduce(self, l):
+        out = (C.c_double * 4)()
+        self._check(lib().lbm_reduce(self._h, l, out))
+        return np.array(out[:])
+
+    def check_status(self):
+        self._check(lib().lbm_check_status(self._h))
+
+    def max_newton_iters(self):
+        return lib().lbm_max_newton_iters(self._h)
+
+    def timing_enable(self, on=True):
+        self._check(lib().lbm_timing_enable(self._h, int(on)))
+
+    def timing_read(self):
+        ms = (C.c_double * MAX_LEVELS)()
+        n = (C.c_int64 * MAX_LEVELS)()
+        self._check(lib().lbm_timing_read(self._h, ms, n))
+        return list(ms[: self.n_levels]), list(n[: self.n_levels])
+
+    def launch_count(self):
+        return lib().lbm_launch_count(self._h)
+
+    def device_bytes(self):
+        return lib().lbm_device_bytes(self._h)
+
+    def synchronize(self):
+        self._check(lib().lbm_synchronize(self._h))

@@ -1,0 +1,82 @@
+"""The C-ABI library loads and exports every entry point include/lbm.h declares,
+and host-side validation rejects malformed descriptions before any device work
+(no GPU needed)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2004_14887_gb300 import build as B
+from paper_2004_14887_gb300 import lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return lbm.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    return sorted(set(re.findall(r"LBM_API\s+[\w\s\*]+?\b(lbm_\w+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = _declared()
+    assert len(names) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", lbm.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\b(lbm_\w+)\b", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(L, n)
+    # the binding knows every declared entry point
+    assert set(names) <= set(lbm.EXPORTS)
+
+
+def test_library_is_built_for_sm_103a(L):
+    """The build targets sm_103a only, with no PTX for other architectures."""
+    assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_desc_struct_layout_matches_header(L):
+    """Field offsets of the ctypes mirror follow the C declaration order and alignment."""
+    d = lbm.lbm_hierarchy_desc
+    assert d.coarse_n.offset == 8
+    assert d.box_lo.offset == 32
+    assert d.box_hi.offset == 32 + 96
+    assert d.nu0.offset == 32 + 192
+    assert d.alloc.offset % 8 == 0
+    assert C.sizeof(d) == d.alloc_ctx.offset + 8
+
+
+@pytest.mark.parametrize("bad,match", [
+    ({"lattice": 7}, "lattice"),
+    ({"boxes": [((30, 30), (40, 40))]}, "margin|seam"),
+    ({"boxes": [((10, 10), (11, 11))]}, "4 parent cells"),
+    ({"boxes": [((8, 8), (24, 24)), ((9, 9), (20, 20))]}, "margin"),
+    ({"nu0": -1.0}, "nu0"),
+    ({"dc_variant": 3}, "dc_variant"),
+])
+def test_malformed_descriptions_are_rejected_on_the_host(L, bad, match):
+    desc = {"lattice": 9, "coarse_n": (32, 32), "boxes": [((8, 8), (24, 24))], "nu0": 1e-5}
+    desc.update(bad)
+    d = lbm.make_desc(desc)
+    h = C.c_void_p()
+    rc = L.lbm_create_hierarchy(C.byref(d), None, C.byref(h))
+    assert rc == lbm.LBM_ERR_BAD_DESC
+    assert not h.value
+    assert re.search(match, L.lbm_create_error().decode())
+
+
+def test_binding_refuses_without_gpu():
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(RuntimeError, match="CUDA device"):
+        lbm.Hierarchy({"lattice": 9, "coarse_n": (32, 32), "boxes": [], "nu0": 1e-5})
