@@ -128,13 +128,10 @@ __device__ __forceinline__ void node_coords(const LevelGeo &g, long long idx, in
 // wrap (periodic) or reject a coordinate; returns false outside a non-periodic box
 __device__ __forceinline__ bool wrap_coord(int &v, int n, int per)
 {
-    if (v < 0) {
-        if (!per) return false;
-        v += n;
-    } else if (v >= n) {
-        if (!per) return false;
-        v -= n;
-    }
+    if (v >= 0 && v < n) return true;
+    if (!per) return false;
+    v %= n;  // any distance: ragged tiles may sit more than one period past a short axis
+    if (v < 0) v += n;
     return true;
 }
 

@@ -245,6 +245,51 @@ __global__ void k_ie(IfaceDev I, LevelDev F, const S *__restrict__ ff)
     }
 }
 
+// rho, u of the node at box coordinates (xx, yy, zz) for the shared-memory halo:
+// wraps periodic axes, pulls bulk nodes, reads interface nodes from the table;
+// returns false (and rho = 1, u = 0) off a non-periodic box or in the hole.
+template <int Q, typename S>
+__device__ __forceinline__ bool halo_macros(const LevelDev &Lv, const S *__restrict__ fsrc, int xx, int yy, int zz,
+                                            typename St<S>::R &hr, typename St<S>::R *hu)
+{
+    using L = Lat<Q>;
+    using R = typename St<S>::R;
+    constexpr int D = L::D;
+    const LevelGeo &g = Lv.g;
+    hr = R(1);
+    hu[0] = hu[1] = hu[2] = R(0);
+    if (!(wrap_coord(xx, g.n[0], g.per[0]) && wrap_coord(yy, g.n[1], g.per[1]) && wrap_coord(zz, g.n[2], g.per[2])))
+        return false;
+    const long long hidx = node_index(g, xx, yy, zz);
+    const int htag = Lv.tag[hidx];
+    if (htag == TAG_BULK) {
+        R m[3] = {R(0), R(0), R(0)};
+        hr = R(0);
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            int sx = xx - L::c(i, 0), sy = yy - L::c(i, 1), sz = zz - L::c(i, 2);
+            if (!wrap_coord(sx, g.n[0], g.per[0])) sx = xx;  // bulk sources are nodes: never taken
+            if (!wrap_coord(sy, g.n[1], g.per[1])) sy = yy;
+            if (!wrap_coord(sz, g.n[2], g.per[2])) sz = zz;
+            const R v = St<S>::ld(fsrc, (long long)i * g.pitch + node_index(g, sx, sy, sz), L::w(i));
+            hr += v;
+#pragma unroll
+            for (int a = 0; a < D; a++)
+                if (L::c(i, a) != 0) m[a] += R(L::c(i, a)) * v;
+        }
+#pragma unroll
+        for (int a = 0; a < D; a++) hu[a] = m[a] / hr;
+        return true;
+    }
+    if (htag >= 0) {
+        hr = (R)Lv.if_mac[htag];
+#pragma unroll
+        for (int a = 0; a < D; a++) hu[a] = (R)Lv.if_mac[(long long)(1 + a) * Lv.nif + htag];
+        return true;
+    }
+    return false;
+}
+
 // ------------------------------------------------------------------ bulk collide-and-stream
 // One CTA per tile of TX x TY (x TZ) nodes.  Every node of the tile and of its
 // one-node halo pulls its post-stream populations (or reads them from the
@@ -323,6 +368,14 @@ __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__res
 #pragma unroll
         for (int a = 0; a < D; a++) u[a] = (R)Lv.if_mac[(long long)(1 + a) * Lv.nif + tag];
     }
+    if (flag != TILE_FAST && !inside) {
+        // a ragged last tile: on a periodic axis this position is the wrapped node
+        R hr, hu[3];
+        halo_macros<Q, S>(Lv, fsrc, x, y, z, hr, hu);
+        rho = hr;
+#pragma unroll
+        for (int a = 0; a < D; a++) u[a] = hu[a];
+    }
     s_rho[hself] = rho;
 #pragma unroll
     for (int a = 0; a < D; a++) s_u[a][hself] = u[a];
@@ -349,32 +402,8 @@ __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__res
             }
 #pragma unroll
             for (int a = 0; a < D; a++) hu[a] = m[a] / hr;
-        } else if (wrap_coord(xx, g.n[0], g.per[0]) && wrap_coord(yy, g.n[1], g.per[1]) &&
-                   wrap_coord(zz, g.n[2], g.per[2])) {
-            const long long hidx = node_index(g, xx, yy, zz);
-            const int htag = Lv.tag[hidx];
-            if (htag == TAG_BULK) {
-                R m[3] = {R(0), R(0), R(0)};
-                hr = R(0);
-#pragma unroll
-                for (int i = 0; i < Q; i++) {
-                    int sx = xx - L::c(i, 0), sy = yy - L::c(i, 1), sz = zz - L::c(i, 2);
-                    if (!wrap_coord(sx, g.n[0], g.per[0])) sx = xx;  // bulk sources are nodes: never taken
-                    if (!wrap_coord(sy, g.n[1], g.per[1])) sy = yy;
-                    if (!wrap_coord(sz, g.n[2], g.per[2])) sz = zz;
-                    const R v = St<S>::ld(fsrc, (long long)i * g.pitch + node_index(g, sx, sy, sz), L::w(i));
-                    hr += v;
-#pragma unroll
-                    for (int a = 0; a < D; a++)
-                        if (L::c(i, a) != 0) m[a] += R(L::c(i, a)) * v;
-                }
-#pragma unroll
-                for (int a = 0; a < D; a++) hu[a] = m[a] / hr;
-            } else if (htag >= 0) {
-                hr = (R)Lv.if_mac[htag];
-#pragma unroll
-                for (int a = 0; a < D; a++) hu[a] = (R)Lv.if_mac[(long long)(1 + a) * Lv.nif + htag];
-            }
+        } else {
+            halo_macros<Q, S>(Lv, fsrc, xx, yy, zz, hr, hu);
         }
         s_rho[h] = hr;
 #pragma unroll
