@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Throughput of the multi-level DC2 / H-RR lattice Boltzmann hot path on GB300.
+
+Workload: the D2Q9 three-level nested-patch acoustic pulse (coarse 512^2
+periodic, patches of 256^2 and 128^2 coarse cells, Mach-0.2 mean flow, pulse
+amplitude 1e-3), FP32 population storage for the headline value, FP64 and FP16
+(shifted) storage reported beside it.  One step = one coarse step = 1 step of
+level 0, 2 of level 1 and 4 of level 2 (1.65 M node updates, 16.8 M
+fine-equivalent updates).  Inputs live in HBM when timing starts; the L2 is
+flushed (256 MB write) before every timed step, outside the timed events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+For N > 1 (torchrun) every rank advances an independent replica of the same
+hierarchy (the single hierarchy does not shard; replicas only); the value is
+the sum of the ranks' node updates over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (fine-equiv) & % HBM roofline, FP32/FP16-shift vs FP64 on same GB300"
+UNIT = "MLUPS (fine-equivalent)"
+BYTES_PER_POP = {"f64": 8, "f32": 4, "f16s": 2}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
+                 "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.12)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _traffic_from_profiles(kernel_key):
+    """DRAM bytes per launch recorded by an ncu capture in profiles/ for this kernel
+    and source revision, or None."""
+    path = os.path.join(ROOT, "profiles", "k_bulk_pulse2d_3lvl_f32.md")
+    if not os.path.exists(path):
+        return None
+    try:
+        from paper_2004_14887_gb300 import build as B
+
+        import hashlib
+
+        h = hashlib.sha1()
+        for s in B.sources() + [os.path.join(B.CSRC, "lbm_kernels.cuh"), os.path.join(B.CSRC, "lbm_device.cuh")]:
+            h.update(open(s, "rb").read())
+        sha = h.hexdigest()[:12]
+        txt = open(path).read()
+        m = re.search(r"traffic_per_full_launch_bytes:\s*([0-9.eE+]+)\s+source_sha:\s*(\w+)", txt)
+        if m and m.group(2) == sha:
+            return float(m.group(1))
+    except Exception:
+        return None
+    return None
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    from paper_2004_14887_gb300 import lbm
+    from paper_2004_14887_gb300 import workloads as W
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        import torch.distributed as dist
+
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+
+    def make(storage, use_graphs=True):
+        d = W.pulse2d(storage=storage)
+        h = lbm.Hierarchy(d, use_graphs=use_graphs)
+        for l in range(h.n_levels):
+            r, u = W.init_fields(d, l)
+            h.init_fields(l, r, u)
+        return d, h
+
+    def timed(h, K, Wm, sampler_dev=None):
+        h.advance(Wm)
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        n0 = h.launch_count()
+        barrier()
+        torch.cuda.synchronize()
+        clocks = None
+        t0 = time.perf_counter()
+        if sampler_dev is not None:
+            with ClockSampler(sampler_dev) as cs:
+                for k in range(K):
+                    flush.zero_()
+                    starts[k].record()
+                    h.advance(1)
+                    ends[k].record()
+                torch.cuda.synchronize()
+            clocks = cs.summary()
+        else:
+            for k in range(K):
+                flush.zero_()
+                starts[k].record()
+                h.advance(1)
+                ends[k].record()
+            torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - t0
+        h.check_status()
+        dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+        return dev_ms, wall, h.launch_count() - n0, clocks
+
+    K, Wm = args.steps, args.warmup
+    d, h = make("f32")
+    upd = W.updates_per_coarse_step(d)
+    feq = W.fine_equivalent_per_coarse_step(d)
+    dev_ms, wall, launches, clocks = timed(h, K, Wm, sampler_dev=local)
+    t = max_over_ranks(dev_ms) / 1e3
+    value = ws * feq * K / t / 1e6
+    actual = ws * upd * K / t / 1e6
+
+    # dominant kernel: the bulk collide-and-stream of the finest level (4 launches per step)
+    L = h.n_levels
+    h.timing_enable(True)
+    Kt = min(K, 200)
+    for _ in range(Kt):
+        flush.zero_()
+        h.advance(1)
+    ms, cnt = h.timing_read()
+    h.timing_enable(False)
+    bulk_ms = [m / max(c, 1) for m, c in zip(ms, cnt)]
+    nact = [h.levels[l]["n_active"] for l in range(L)]
+    bytes_finest = nact[L - 1] * 2 * h.q * BYTES_PER_POP["f32"]
+    peak, peak_src = _peaks()
+    achieved = bytes_finest / (bulk_ms[L - 1] * 1e-3) / 1e9
+
+    # reduced / full precision variants on the same workload
+    variants = {}
+    if not args.no_variants:
+        for st in ("f64", "f16s"):
+            dv, hv = make(st)
+            Kv = min(K, 400 if st == "f64" else K)
+            dms, _, _, _ = timed(hv, Kv, max(3, Wm // 2))
+            tv = max_over_ranks(dms) / 1e3
+            hv.timing_enable(True)
+            for _ in range(min(Kv, 100)):
+                flush.zero_()
+                hv.advance(1)
+            msv, cntv = hv.timing_read()
+            hv.timing_enable(False)
+            bl = msv[L - 1] / max(cntv[L - 1], 1)
+            variants[st] = {
+                "value": ws * feq * Kv / tv / 1e6, "actual_mlups": ws * upd * Kv / tv / 1e6,
+                "ms_per_step": 1e3 * tv / Kv, "steps": Kv,
+                "finest_bulk_gbs": nact[L - 1] * 2 * h.q * BYTES_PER_POP[st] / (bl * 1e-3) / 1e9,
+            }
+            hv.close()
+            del hv
+        variants["f32_speedup_vs_f64"] = value / variants["f64"]["value"]
+        variants["f16s_speedup_vs_f64"] = variants["f16s"]["value"] / variants["f64"]["value"]
+
+    # end to end through the public API with host buffers: init (H2D), K steps, macros (D2H)
+    e2e = None
+    if not args.no_e2e:
+        de = W.pulse2d(storage="f32")
+        he = lbm.Hierarchy(de)
+        fields = []
+        for l in range(he.n_levels):
+            r, u = W.init_fields(de, l)
+            rp = torch.from_numpy(r).pin_memory().numpy()
+            up = torch.from_numpy(u).pin_memory().numpy()
+            fields.append((rp, up))
+        outs = [(torch.empty(he.levels[l]["N"], dtype=torch.float64).pin_memory().numpy(),
+                 torch.empty((2, he.levels[l]["N"]), dtype=torch.float64).pin_memory().numpy())
+                for l in range(he.n_levels)]
+        he.advance(3)
+        torch.cuda.synchronize()
+        barrier()
+        te = time.perf_counter()
+        for l in range(he.n_levels):
+            he.init_fields(l, *fields[l])
+        he.advance(K)
+        for l in range(he.n_levels):
+            he.get_macros(l, out=outs[l])
+        torch.cuda.synchronize()
+        barrier()
+        tw = max_over_ranks(time.perf_counter() - te)
+        h2d = sum(a.nbytes + b.nbytes for a, b in fields)
+        d2h = sum(a.nbytes + b.nbytes for a, b in outs)
+        e2e = {"value": ws * feq * K / tw / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
+               "d2h_bytes_per_step": d2h / K}
+        he.close()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
+        "ms_per_step": 1e3 * t / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded analytic pulse, no dataset)",
+        "config": {"workload": "pulse2d_3lvl: D2Q9, 3 levels, coarse 512^2 periodic, patches 256^2 and 128^2 "
+                               "coarse cells, Mach 0.2, A=1e-3, FP32 storage", "levels": L,
+                   "node_updates_per_step": upd, "fine_equivalent_updates_per_step": feq,
+                   "active_nodes_per_level": nact, "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+        "actual_mlups": actual,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": _traffic_from_profiles("k_bulk"), "kernel": "k_bulk<9,float> level 2",
+                     "algorithmic_bytes_per_launch": bytes_finest, "avg_launch_ms": bulk_ms[L - 1],
+                     "peak_source": f"{peak_src} hbm_gbs"},
+        "bulk_ms_per_launch_by_level": bulk_ms,
+        "step_roofline_frac": (upd * 2 * h.q * 4) / (t / K) / 1e9 / peak,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+        "variants": variants,
+    }
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
+    h.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def _replica_desc():
+    """The 1/16-size replica of the benchmark workload (128^2 coarse, same
+    proportions and physics) on which the CPU oracle is timed."""
+    from paper_2004_14887_gb300 import workloads as W
+
+    return W.pulse2d(n=128, boxes=((32, 96), (48, 80)), steps=20)
+
+
+def cpu_baseline(steps):
+    from oracle import oracle as O
+    from paper_2004_14887_gb300 import workloads as W
+
+    d = _replica_desc()
+    o = O.Hierarchy(d)
+    for l in range(o.n_levels):
+        r, u = W.init_fields(d, l)
+        o.init(l, r, u)
+    o.advance(1)
+    t0 = time.perf_counter()
+    o.advance(steps)
+    dt = time.perf_counter() - t0
+    feq = W.fine_equivalent_per_coarse_step(d)
+    return {"value": feq * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} coarse steps of the 128^2 three-level replica of the workload "
+                      f"({W.updates_per_coarse_step(d)} node updates per step), single-threaded FP64 oracle",
+            "actual_mlups": W.updates_per_coarse_step(d) * steps / dt / 1e6}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2004_14887_gb300 import workloads as W
+
+    d = _replica_desc()
+    o = O.Hierarchy(d)
+    for l in range(o.n_levels):
+        r, u = W.init_fields(d, l)
+        o.init(l, r, u)
+    o.advance(args.warmup)
+    K = args.steps
+    t0 = time.perf_counter()
+    o.advance(K)
+    dt = time.perf_counter() - t0
+    feq = W.fine_equivalent_per_coarse_step(d)
+    v = feq * K / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": K,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded analytic pulse, no dataset)",
+            "config": {"workload": "pulse2d_3lvl replica: D2Q9, 3 levels, coarse 128^2, patches 64^2 and 32^2 coarse "
+                                   "cells (1/16 of the 512^2 workload, same proportions and physics)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{K} coarse steps of the 128^2 replica, single-threaded FP64 oracle"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=150)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()
