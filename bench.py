@@ -138,6 +138,8 @@ def run_gb300(args):
 
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
+    # one non-default stream for the library, the L2 flushes and the timing events
+    torch.cuda.set_stream(torch.cuda.Stream())
     if ws > 1:
         import torch.distributed as dist
 

@@ -104,10 +104,10 @@ struct LevelDev {
     const int *tag;          // per node: TAG_BULK, TAG_HOLE or interface-table index
     const unsigned char *tile_flag;
     int tiles[3];
-    double *if_pop;          // interface table: completed post-stream populations [Q][nif]
-    double *if_mac;          // rho, ux, uy, uz [4][nif]
-    double *if_S;            // strain rate [6][nif]
-    double *if_C;            // C_ab = sum_g d_g Psi_abg [6][nif]
+    void *if_pop;            // interface table (type R): completed post-stream populations [Q][nif]
+    void *if_mac;            // rho, ux, uy, uz [4][nif]
+    void *if_S;              // strain rate [6][nif]
+    void *if_C;              // C_ab = sum_g d_g Psi_abg [6][nif]
     int nif;
     double tau;
 };
@@ -280,7 +280,7 @@ __device__ __forceinline__ void hrr_collide(R (&f)[Q], R rho, const R *u, const 
     }
 }
 
-// Equilibrium of Eq. (fEq_herm) and its derivatives with respect to X = (rho, u)
+// Equilibrium of Eq. (fEq_herm) of population i
 template <int Q>
 __device__ __forceinline__ double feq_one(int i, double rho, const double *u)
 {
@@ -296,92 +296,6 @@ __device__ __forceinline__ double feq_one(int i, double rho, const double *u)
         for (int b = 0; b < D; b++)
             if (a != b) h3 += (L::c(i, a) * L::c(i, a) - cs2) * L::c(i, b) * u[a] * u[a] * u[b];
     return L::w(i) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu + 13.5 * h3);
-}
-
-template <int Q>
-__device__ __forceinline__ void dfeq_one(int i, double rho, const double *u, double feq, double *d)
-{
-    using L = Lat<Q>;
-    constexpr int D = L::D;
-    const double cs2 = 1.0 / 3.0;
-    double cu = 0.0;
-    for (int a = 0; a < D; a++) cu += L::c(i, a) * u[a];
-    d[0] = feq / rho;
-    for (int g = 0; g < D; g++) {
-        double t = 3.0 * L::c(i, g) + 9.0 * cu * L::c(i, g) - 3.0 * u[g];
-        double h = 0.0;
-        for (int b = 0; b < D; b++)
-            if (b != g) h += (L::c(i, g) * L::c(i, g) - cs2) * L::c(i, b) * 2.0 * u[g] * u[b];
-        for (int a = 0; a < D; a++)
-            if (a != g) h += (L::c(i, a) * L::c(i, a) - cs2) * L::c(i, g) * u[a] * u[a];
-        d[1 + g] = L::w(i) * rho * (t + 13.5 * h);
-    }
-}
-
-// Newton-Raphson for F(X) = sum_i Gamma_i Phi_i (fhat_i - f0_i(X)) = 0 (Eq. system_fi),
-// started from the plain moments of fhat, stopped once max|dX| < 1e-12 (Eq. updated_macro).
-template <int Q>
-__device__ int newton_solve(const double *fhat, const double *Gam, double *X)
-{
-    using L = Lat<Q>;
-    constexpr int D = L::D, n = D + 1;
-    double rho = 0.0, m[3] = {0.0, 0.0, 0.0};
-    for (int i = 0; i < Q; i++) {
-        rho += fhat[i];
-        for (int a = 0; a < D; a++) m[a] += L::c(i, a) * fhat[i];
-    }
-    X[0] = rho;
-    for (int a = 0; a < 3; a++) X[1 + a] = a < D ? m[a] / rho : 0.0;
-    for (int it = 1; it <= 10; it++) {
-        double F[4] = {0, 0, 0, 0}, J[16];
-        for (int k = 0; k < 16; k++) J[k] = 0.0;
-        for (int i = 0; i < Q; i++) {
-            const double fe = feq_one<Q>(i, X[0], X + 1);
-            double d[4];
-            dfeq_one<Q>(i, X[0], X + 1, fe, d);
-            double phi[4] = {1.0, (double)L::c(i, 0), (double)L::c(i, 1), D == 3 ? (double)L::c(i, 2) : 0.0};
-            for (int r = 0; r < n; r++) {
-                F[r] += Gam[i] * phi[r] * (fhat[i] - fe);
-                for (int k = 0; k < n; k++) J[r * n + k] -= Gam[i] * phi[r] * d[k];
-            }
-        }
-        // Gaussian elimination with partial pivoting on J dX = -F
-        double b[4], dX[4];
-        for (int r = 0; r < n; r++) b[r] = -F[r];
-        for (int k = 0; k < n; k++) {
-            int p = k;
-            for (int r = k + 1; r < n; r++)
-                if (fabs(J[r * n + k]) > fabs(J[p * n + k])) p = r;
-            if (J[p * n + k] == 0.0) return -1;
-            if (p != k) {
-                for (int c2 = 0; c2 < n; c2++) {
-                    double t = J[k * n + c2];
-                    J[k * n + c2] = J[p * n + c2];
-                    J[p * n + c2] = t;
-                }
-                double t = b[k];
-                b[k] = b[p];
-                b[p] = t;
-            }
-            for (int r = k + 1; r < n; r++) {
-                double mlt = J[r * n + k] / J[k * n + k];
-                for (int c2 = k; c2 < n; c2++) J[r * n + c2] -= mlt * J[k * n + c2];
-                b[r] -= mlt * b[k];
-            }
-        }
-        for (int k = n - 1; k >= 0; k--) {
-            double s = b[k];
-            for (int c2 = k + 1; c2 < n; c2++) s -= J[k * n + c2] * dX[c2];
-            dX[k] = s / J[k * n + k];
-        }
-        double mx = 0.0;
-        for (int r = 0; r < n; r++) {
-            X[r] += dX[r];
-            mx = fmax(mx, fabs(dX[r]));
-        }
-        if (mx < 1e-12) return it;
-    }
-    return -1;
 }
 
 }  // namespace lbmg

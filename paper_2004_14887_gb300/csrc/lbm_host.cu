@@ -47,12 +47,13 @@ struct Level {
     void *f[2] = {nullptr, nullptr};
     int *d_tag = nullptr;
     unsigned char *d_tile = nullptr;
-    double *if_pop = nullptr, *if_mac = nullptr, *if_S = nullptr, *if_C = nullptr;
+    void *if_pop = nullptr, *if_mac = nullptr, *if_S = nullptr, *if_C = nullptr;
     double *d_wnode = nullptr;
 };
 
 struct Iface {  // between coarse level l-1 and fine level l
-    std::vector<long long> tf_fine, tf_coarse, ie_fine, ring_coarse, tf_ridx;
+    std::vector<long long> tf_fine, tf_coarse, ie_fine, ring_coarse;
+    std::vector<int> tf_ridx;
     std::vector<unsigned int> tf_kf, tf_kc, tf_gc, ie_kf;
     std::vector<signed char> tf_rkind;
     std::vector<int> ie_nst, ie_st;
@@ -159,6 +160,20 @@ int64_t emod(int64_t a, int64_t n)
 int lat_c(int Q, int i, int a) { return Q == 9 ? Lat<9>::c(i, a) : Lat<19>::c(i, a); }
 
 size_t store_size(int storage) { return storage == LBM_F64 ? 8 : (storage == LBM_F32 ? 4 : 2); }
+// arithmetic type of the storage: FP64 for FP64 storage, FP32 otherwise
+size_t arith_size(int storage) { return storage == LBM_F64 ? 8 : 4; }
+
+// box coordinates of linear indices, [n][3] int32
+std::vector<int> coords3(const Level &v, const std::vector<long long> &idx)
+{
+    std::vector<int> out(idx.size() * 3);
+    for (size_t k = 0; k < idx.size(); k++) {
+        out[3 * k] = (int)(idx[k] % v.n[0]);
+        out[3 * k + 1] = (int)((idx[k] / v.n[0]) % v.n[1]);
+        out[3 * k + 2] = (int)(idx[k] / (v.n[0] * v.n[1]));
+    }
+    return out;
+}
 
 // linear index of global level-l coordinates p, or -1 if not a node of level l
 long long node_of(const lbm_h h, int l, const int64_t *p)
@@ -343,7 +358,7 @@ int build_interfaces(lbm_h h)
                             I.tf_ridx[k] = tf_of[j];
                         } else if (F.cls[j] == LBM_NODE_BULK) {
                             I.tf_rkind[k] = RK_FINE;
-                            I.tf_ridx[k] = j;
+                            I.tf_ridx[k] = (int)j;
                         } else {
                             return fail(nullptr, LBM_ERR_BAD_DESC, "TF gradient stencil meets a non-bulk fine node");
                         }
@@ -520,17 +535,17 @@ int upload_all(lbm_h h)
         }
         v.d_tag = upload(h, v.tag, &ok);
         v.d_tile = upload(h, v.tile_flag, &ok);
-        const size_t ni = std::max(1, v.nif);
-        v.if_pop = (double *)dev_alloc(h, ni * Q * sizeof(double));
-        v.if_mac = (double *)dev_alloc(h, ni * 4 * sizeof(double));
-        v.if_S = (double *)dev_alloc(h, ni * 6 * sizeof(double));
-        v.if_C = (double *)dev_alloc(h, ni * 6 * sizeof(double));
+        const size_t ni = std::max(1, v.nif), as = arith_size(h->d.storage);
+        v.if_pop = dev_alloc(h, ni * Q * as);
+        v.if_mac = dev_alloc(h, ni * 4 * as);
+        v.if_S = dev_alloc(h, ni * 6 * as);
+        v.if_C = dev_alloc(h, ni * 6 * as);
         v.d_wnode = upload(h, node_weights(h, l), &ok);
         if (!ok || !v.if_pop || !v.if_mac || !v.if_S || !v.if_C) return fail(h, LBM_ERR_OOM, "tables of level %d", l);
-        CK(cudaMemset(v.if_pop, 0, ni * Q * sizeof(double)));
-        CK(cudaMemset(v.if_mac, 0, ni * 4 * sizeof(double)));
-        CK(cudaMemset(v.if_S, 0, ni * 6 * sizeof(double)));
-        CK(cudaMemset(v.if_C, 0, ni * 6 * sizeof(double)));
+        CK(cudaMemset(v.if_pop, 0, ni * Q * as));
+        CK(cudaMemset(v.if_mac, 0, ni * 4 * as));
+        CK(cudaMemset(v.if_S, 0, ni * 6 * as));
+        CK(cudaMemset(v.if_C, 0, ni * 6 * as));
     }
     for (int l = 1; l < h->nl; l++) {
         Iface &I = h->ifc[l];
@@ -538,21 +553,21 @@ int upload_all(lbm_h h)
         g.nTF = (int)I.tf_fine.size();
         g.nIE = (int)I.ie_fine.size();
         g.nRing = (int)I.ring_coarse.size();
-        g.tf_fine = upload(h, I.tf_fine, &ok);
-        g.tf_coarse = upload(h, I.tf_coarse, &ok);
+        g.tf_f = upload(h, coords3(h->lev[l], I.tf_fine), &ok);
+        g.tf_c = upload(h, coords3(h->lev[l - 1], I.tf_coarse), &ok);
         g.tf_kf = upload(h, I.tf_kf, &ok);
         g.tf_kc = upload(h, I.tf_kc, &ok);
         g.tf_gc = upload(h, I.tf_gc, &ok);
         g.tf_rkind = upload(h, I.tf_rkind, &ok);
         g.tf_ridx = upload(h, I.tf_ridx, &ok);
-        g.ie_fine = upload(h, I.ie_fine, &ok);
+        g.ie_f = upload(h, coords3(h->lev[l], I.ie_fine), &ok);
         g.ie_kf = upload(h, I.ie_kf, &ok);
         g.ie_nst = upload(h, I.ie_nst, &ok);
         g.ie_st = upload(h, I.ie_st, &ok);
         g.ie_w = upload(h, I.ie_w, &ok);
-        g.ring_coarse = upload(h, I.ring_coarse, &ok);
-        g.hist_f = (double *)dev_alloc(h, (size_t)3 * Q * std::max(1, g.nTF) * sizeof(double));
-        g.hist_m = (double *)dev_alloc(h, (size_t)3 * 4 * std::max(1, g.nRing) * sizeof(double));
+        g.ring_c = upload(h, coords3(h->lev[l - 1], I.ring_coarse), &ok);
+        g.hist_f = dev_alloc(h, (size_t)3 * Q * std::max(1, g.nTF) * arith_size(h->d.storage));
+        g.hist_m = dev_alloc(h, (size_t)3 * 4 * std::max(1, g.nRing) * arith_size(h->d.storage));
         g.tfc_base = h->lev[l - 1].nTFP + h->lev[l - 1].nIE;
         g.R = I.R;
         if (!ok || !g.hist_f || !g.hist_m) return fail(h, LBM_ERR_OOM, "interface %d tables", l);
@@ -610,12 +625,14 @@ struct Sched {
             }
             cudaEventRecord(h->ev_pool[ev], h->stream);
         }
+        using R = typename St<S>::R;
+        const R tau = (R)v.tau, sig = (R)h->d.sigma, sps = (R)spsi;
         if constexpr (Lat<Q>::D == 2)
-            k_bulk<Q, S, T2X, T2Y, 1><<<nt, T2X * T2Y, 0, h->stream>>>(level_dev(h, l), (const S *)src, (S *)dst,
-                                                                      h->d.sigma, spsi);
+            k_bulk<Q, S, T2X, T2Y, 1><<<nt, T2X * T2Y, 0, h->stream>>>(level_dev(h, l), (const S *)src, (S *)dst, tau,
+                                                                      sig, sps);
         else
             k_bulk<Q, S, T3X, T3Y, T3Z><<<nt, T3X * T3Y * T3Z, 0, h->stream>>>(level_dev(h, l), (const S *)src,
-                                                                              (S *)dst, h->d.sigma, spsi);
+                                                                              (S *)dst, tau, sig, sps);
         h->launch_counter++;
         if (h->timing) {
             cudaEventRecord(h->ev_pool[ev + 1], h->stream);
@@ -651,13 +668,13 @@ struct Sched {
         Level &v = h->lev[l];
         const void *fA = v.f[k & 1];
         void *fB = v.f[(k + 1) & 1];
-        const int B = 128;
+        const int B = 32;  // one warp per block: O(surface) work spread over many SMs
         LevelDev dv = level_dev(h, l);
         if (l + 1 < h->nl) {
             const IfaceDev &I = h->ifc[l + 1].dev;
             const int n = I.nTF + I.nRing;
             if (n > 0) {
-                k_hist<Q, S><<<(n + B - 1) / B, B, 0, h->stream>>>(I, dv.g, (const S *)fA, (int)((k + 1) % 3));
+                k_hist<Q, S><<<(n + B - 1) / B, B, 0, h->stream>>>(I, dv.g, (const S *)fA, (int)((k + 1) % 3), 0);
                 h->launch_counter++;
             }
         }
@@ -666,8 +683,9 @@ struct Sched {
             tw = weights(phase, kp);
             const IfaceDev &I = h->ifc[l].dev;
             if (I.nTF > 0) {
-                k_recon<Q, S><<<(I.nTF + B - 1) / B, B, 0, h->stream>>>(I, dv, level_dev(h, l - 1), (const S *)fA,
-                                                                       tw, phase, h->d_status, h->d_maxit);
+                constexpr int per_block = 128 / (Q <= 16 ? 16 : 32);
+                k_recon<Q, S><<<(I.nTF + per_block - 1) / per_block, 128, 0, h->stream>>>(
+                    I, dv, level_dev(h, l - 1), (const S *)fA, tw, phase, h->d_status, h->d_maxit);
                 h->launch_counter++;
             }
         }
@@ -702,7 +720,7 @@ struct Sched {
         if (l + 1 < h->nl) {
             const IfaceDev &I = h->ifc[l + 1].dev;
             const int n = I.nTF + I.nRing;
-            if (n > 0) k_hist_seed<Q, S><<<(n + 127) / 128, 128, 0, h->stream>>>(I, dv.g, (const S *)v.f[0]);
+            if (n > 0) k_hist<Q, S><<<(n + 31) / 32, 32, 0, h->stream>>>(I, dv.g, (const S *)v.f[0], 0, 1);
         }
         return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
     }

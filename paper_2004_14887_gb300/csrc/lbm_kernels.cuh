@@ -6,27 +6,27 @@
 namespace lbmg {
 
 // ------------------------------------------------------------------ interface views
+// Interface tables hold values in the arithmetic type R of the storage (double
+// for FP64 storage, float for FP32 and FP16-shifted storage); the
+// equilibrium/non-equilibrium rescalings of Eqs. (rescff) and (rescfc) are
+// evaluated in FP64 in every mode.
 struct IfaceDev {
     int nTF, nIE, nRing;
-    // TF nodes: fine node index (level f), coarse node index (level c), population masks
-    const long long *tf_fine;
-    const long long *tf_coarse;
-    const unsigned int *tf_kf;      // fine-known
-    const unsigned int *tf_kc;      // coarse-known
+    const int *tf_f;                // [nTF][3] fine-level box coordinates of TF nodes
+    const int *tf_c;                // [nTF][3] coarse-level box coordinates
+    const unsigned int *tf_kf;      // fine-known populations
+    const unsigned int *tf_kc;      // coarse-known populations
     const unsigned int *tf_gc;      // gamma_i = c (Table 1)
     const signed char *tf_rkind;    // [nTF][2D] gradient stencil reference kind
-    const long long *tf_ridx;       // [nTF][2D] reference index (fine node / TF / ring)
-    // hanging nodes
-    const long long *ie_fine;
+    const int *tf_ridx;             // [nTF][2D] reference: fine node index / TF index / ring index
+    const int *ie_f;                // [nIE][3] fine-level box coordinates of hanging nodes
     const unsigned int *ie_kf;
     const int *ie_nst;
     const int *ie_st;               // [nIE][16] TF indices
     const double *ie_w;             // [nIE][16]
-    // ring of coarse stencil nodes
-    const long long *ring_coarse;
-    // history: coarse post-stream populations at TF [3][Q][nTF], ring macros [3][4][nRing]
-    double *hist_f;
-    double *hist_m;
+    const int *ring_c;              // [nRing][3] coarse-level box coordinates
+    void *hist_f;                   // [3][Q][nTF] coarse post-stream populations at TF nodes (type R)
+    void *hist_m;                   // [3][4][nRing] coarse post-stream macros on the ring (type R)
     int tfc_base;                   // table index of the first TF node in the coarse level's table
     double R;                       // Eq. (fneqResc): R = tau_f / (2 tau_c)
 };
@@ -36,116 +36,310 @@ struct TimeW {
     double w[3];   // weights (Eq. TempInt, linear on the first coarse step, [0,0,1] on sync)
 };
 
+__device__ __forceinline__ int box_index(const LevelGeo &g, int x, int y, int z)
+{
+    return x + g.n[0] * (y + g.n[1] * z);
+}
+
+// index of (x,y,z) + (dx,dy,dz) with periodic wrap, -1 off a non-periodic box
+__device__ __forceinline__ int nb_index(const LevelGeo &g, int x, int y, int z, int dx, int dy, int dz)
+{
+    x += dx;
+    y += dy;
+    z += dz;
+    if (!wrap_coord(x, g.n[0], g.per[0]) || !wrap_coord(y, g.n[1], g.per[1]) || !wrap_coord(z, g.n[2], g.per[2]))
+        return -1;
+    return box_index(g, x, y, z);
+}
+
+// post-stream moments of a node whose Q sources are all nodes of the level (pull)
+template <int Q, typename S>
+__device__ __forceinline__ void pulled_moments(const LevelGeo &g, const S *__restrict__ f, int x, int y, int z,
+                                               typename St<S>::R &rho, typename St<S>::R *u)
+{
+    using L = Lat<Q>;
+    using R = typename St<S>::R;
+    constexpr int D = L::D;
+    R r = R(0), m[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const int s = nb_index(g, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
+        const R v = s >= 0 ? St<S>::ld(f, (long long)i * g.pitch + s, L::w(i)) : R(0);
+        r += v;
+#pragma unroll
+        for (int a = 0; a < D; a++)
+            if (L::c(i, a) != 0) m[a] += R(L::c(i, a)) * v;
+    }
+    rho = r;
+#pragma unroll
+    for (int a = 0; a < 3; a++) u[a] = a < D ? m[a] / r : R(0);
+}
+
 // ------------------------------------------------------------------ history push
 // post-stream coarse populations at TF nodes (coarse-known ones) and post-stream
 // macros at ring nodes, for the child level's Eq. (TempInt)
 template <int Q, typename S>
-__global__ void k_hist(IfaceDev I, LevelGeo gc, const S *__restrict__ fc, int slot)
+__global__ void k_hist(IfaceDev I, LevelGeo gc, const S *__restrict__ fc, int slot, int seed)
 {
     using L = Lat<Q>;
+    using R = typename St<S>::R;
     constexpr int D = L::D;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    R *hf = (R *)I.hist_f;
+    R *hm = (R *)I.hist_m;
     if (t < I.nTF) {
-        const long long idx = I.tf_coarse[t];
+        const int x = I.tf_c[3 * t], y = I.tf_c[3 * t + 1], z = I.tf_c[3 * t + 2];
         const unsigned int kc = I.tf_kc[t];
+#pragma unroll
         for (int i = 0; i < Q; i++) {
-            double v = 0.0;
-            if ((kc >> i) & 1u) {
-                const long long s = shifted_index(gc, idx, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
-                if (s >= 0) v = (double)St<S>::ld(fc, (long long)i * gc.pitch + s, L::w(i));
+            R v = R(0);
+            // seed: slot 0 holds the initial state itself; otherwise the post-stream value
+            const int s = seed ? box_index(gc, x, y, z)
+                               : (((kc >> i) & 1u) ? nb_index(gc, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2)) : -1);
+            if (s >= 0) v = St<S>::ld(fc, (long long)i * gc.pitch + s, L::w(i));
+            hf[((long long)slot * Q + i) * I.nTF + t] = v;
+        }
+    } else if (t < I.nTF + I.nRing) {
+        const int r = t - I.nTF;
+        const int x = I.ring_c[3 * r], y = I.ring_c[3 * r + 1], z = I.ring_c[3 * r + 2];
+        R rho, u[3];
+        if (seed) {
+            R m[3] = {R(0), R(0), R(0)};
+            rho = R(0);
+            const int s = box_index(gc, x, y, z);
+#pragma unroll
+            for (int i = 0; i < Q; i++) {
+                const R v = St<S>::ld(fc, (long long)i * gc.pitch + s, L::w(i));
+                rho += v;
+#pragma unroll
+                for (int a = 0; a < D; a++)
+                    if (L::c(i, a) != 0) m[a] += R(L::c(i, a)) * v;
             }
-            I.hist_f[((long long)slot * Q + i) * I.nTF + t] = v;
+            for (int a = 0; a < 3; a++) u[a] = a < D ? m[a] / rho : R(0);
+        } else {
+            pulled_moments<Q, S>(gc, fc, x, y, z, rho, u);
         }
-    } else if (t < I.nTF + I.nRing) {
-        const int r = t - I.nTF;
-        const long long idx = I.ring_coarse[r];
-        double rho = 0.0, m[3] = {0.0, 0.0, 0.0};
-        for (int i = 0; i < Q; i++) {
-            const long long s = shifted_index(gc, idx, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
-            const double v = s >= 0 ? (double)St<S>::ld(fc, (long long)i * gc.pitch + s, L::w(i)) : 0.0;
-            rho += v;
-            for (int a = 0; a < D; a++) m[a] += L::c(i, a) * v;
-        }
-        double *h = I.hist_m + (long long)slot * 4 * I.nRing;
+        R *h = hm + (long long)slot * 4 * I.nRing;
         h[r] = rho;
-        for (int a = 0; a < 3; a++) h[(long long)(1 + a) * I.nRing + r] = a < D ? m[a] / rho : 0.0;
-    }
-}
-
-// seed slot 0 from the initial state itself (no streaming)
-template <int Q, typename S>
-__global__ void k_hist_seed(IfaceDev I, LevelGeo gc, const S *__restrict__ fc)
-{
-    using L = Lat<Q>;
-    constexpr int D = L::D;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < I.nTF) {
-        const long long idx = I.tf_coarse[t];
-        for (int i = 0; i < Q; i++)
-            I.hist_f[(long long)i * I.nTF + t] = (double)St<S>::ld(fc, (long long)i * gc.pitch + idx, L::w(i));
-    } else if (t < I.nTF + I.nRing) {
-        const int r = t - I.nTF;
-        const long long idx = I.ring_coarse[r];
-        double rho = 0.0, m[3] = {0.0, 0.0, 0.0};
-        for (int i = 0; i < Q; i++) {
-            const double v = (double)St<S>::ld(fc, (long long)i * gc.pitch + idx, L::w(i));
-            rho += v;
-            for (int a = 0; a < D; a++) m[a] += L::c(i, a) * v;
-        }
-        I.hist_m[r] = rho;
-        for (int a = 0; a < 3; a++) I.hist_m[(long long)(1 + a) * I.nRing + r] = a < D ? m[a] / rho : 0.0;
+        for (int a = 0; a < 3; a++) h[(long long)(1 + a) * I.nRing + r] = u[a];
     }
 }
 
 // ------------------------------------------------------------------ TF reconstruction
-// Newton at TF nodes (Eq. system_fi), fine rebuild of gamma=c populations
-// (Eq. rescff), and on sync sub-steps the coarse rebuild of all populations (Eq. rescfc).
-template <int Q, typename S>
-__global__ void k_recon(IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict__ ff, TimeW tw, int sync,
-                        int *status, int *max_iters)
+// segmented warp reduction over the W lanes that hold one TF node's populations
+template <int W, typename T>
+__device__ __forceinline__ T seg_sum(T v)
+{
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, W);
+    return v;
+}
+
+// velocity and weight of a run-time population index
+template <int Q>
+__device__ __forceinline__ void lane_lattice(int i, int &cx, int &cy, int &cz, double &w)
 {
     using L = Lat<Q>;
-    constexpr int D = L::D;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= I.nTF) return;
-    const long long idx = I.tf_fine[t];
-    const unsigned int kf = I.tf_kf[t], gc = I.tf_gc[t];
-    double fhat[Q], Gam[Q];
-    for (int i = 0; i < Q; i++) {
-        if ((gc >> i) & 1u) {
-            double s = 0.0;
-            for (int k = 0; k < 3; k++)
-                if (tw.w[k] != 0.0) s += tw.w[k] * I.hist_f[((long long)tw.slot[k] * Q + i) * I.nTF + t];
-            fhat[i] = s;
-            Gam[i] = I.R;
-        } else {
-            double v = 0.0;
-            if ((kf >> i) & 1u) {
-                const long long s = shifted_index(F.g, idx, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
-                if (s >= 0) v = (double)St<S>::ld(ff, (long long)i * F.g.pitch + s, L::w(i));
+    cx = cy = cz = 0;
+    w = 0.0;
+#pragma unroll
+    for (int j = 0; j < Q; j++)
+        if (i == j) {
+            cx = L::c(j, 0);
+            cy = L::c(j, 1);
+            cz = L::c(j, 2);
+            w = L::w(j);
+        }
+}
+
+// Eq. (fEq_herm) for one population and its derivatives with respect to (rho, u)
+template <int D, typename T>
+__device__ __forceinline__ T feq_lane(const int *c, T w, T rho, const T *u, T *d)
+{
+    const T third = T(1) / T(3);
+    T cu = T(0), uu = T(0), h3 = T(0);
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        cu += T(c[a]) * u[a];
+        uu += u[a] * u[a];
+    }
+    T dh3[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int a = 0; a < D; a++)
+#pragma unroll
+        for (int b = 0; b < D; b++)
+            if (a != b) {
+                const T k = (T(c[a] * c[a]) - third) * T(c[b]);
+                h3 += k * u[a] * u[a] * u[b];
+                dh3[a] += k * T(2) * u[a] * u[b];
+                dh3[b] += k * u[a] * u[a];
             }
-            fhat[i] = v;
-            Gam[i] = 1.0;
+    const T p = T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu + T(13.5) * h3;
+    if (d) {
+        d[0] = w * p;
+#pragma unroll
+        for (int g = 0; g < D; g++)
+            d[1 + g] = w * rho * (T(3) * T(c[g]) + T(9) * cu * T(c[g]) - T(3) * u[g] + T(13.5) * dh3[g]);
+    }
+    return w * rho * p;
+}
+
+// Newton-Raphson for F(X) = sum_i Gamma_i Phi_i (fhat_i - f0_i(X)) = 0 (Eq. system_fi)
+// with one population per lane of a W-lane segment; started from the plain moments
+// of fhat and stopped once max|dX| < tol (Eq. updated_macro).  Every lane of a
+// segment holds the same X.  All 32 lanes of the warp run the same number of
+// iterations (the shuffles need the full warp): a segment that has converged, or
+// is inactive, keeps its X while the others finish.  Returns the iteration count
+// at convergence, or -1 (singular Jacobian or no convergence in 10 iterations).
+template <int Q, int W, typename T>
+__device__ int newton_seg(const int *c, T w, T fhat, T gam, T tol, bool active, T *X)
+{
+    constexpr int D = Lat<Q>::D, n = D + 1;
+    T phi[4] = {T(1), T(c[0]), T(c[1]), T(c[2])};
+    T s[4];
+#pragma unroll
+    for (int r = 0; r < n; r++) s[r] = seg_sum<W>(phi[r] * fhat);
+    X[0] = s[0];
+#pragma unroll
+    for (int a = 0; a < D; a++) X[1 + a] = s[1 + a] / s[0];
+    int done = active ? 0 : 11;  // iteration of convergence; 11 = inactive
+    bool bad = false;
+    for (int it = 1; it <= 10; it++) {
+        T d[4];
+        const T fe = feq_lane<D, T>(c, w, X[0], X + 1, d);
+        T F[4], J[16];
+#pragma unroll
+        for (int r = 0; r < n; r++) {
+            F[r] = seg_sum<W>(gam * phi[r] * (fhat - fe));
+#pragma unroll
+            for (int k = 0; k < n; k++) J[r * n + k] = seg_sum<W>(-gam * phi[r] * d[k]);
+        }
+        // Gaussian elimination with partial pivoting on J dX = -F (same on every lane)
+        T b[4], dX[4];
+        bool sing = false;
+#pragma unroll
+        for (int r = 0; r < n; r++) b[r] = -F[r];
+#pragma unroll
+        for (int k = 0; k < n; k++) {
+            int p = k;
+#pragma unroll
+            for (int r = k + 1; r < n; r++)
+                if (fabs(J[r * n + k]) > fabs(J[p * n + k])) p = r;
+#pragma unroll
+            for (int r = k + 1; r < n; r++)
+                if (r == p) {
+#pragma unroll
+                    for (int c2 = 0; c2 < n; c2++) {
+                        const T t0 = J[k * n + c2];
+                        J[k * n + c2] = J[r * n + c2];
+                        J[r * n + c2] = t0;
+                    }
+                    const T t1 = b[k];
+                    b[k] = b[r];
+                    b[r] = t1;
+                }
+            if (J[k * n + k] == T(0)) {
+                sing = true;
+                J[k * n + k] = T(1);
+            }
+#pragma unroll
+            for (int r = k + 1; r < n; r++) {
+                const T m = J[r * n + k] / J[k * n + k];
+#pragma unroll
+                for (int c2 = k; c2 < n; c2++) J[r * n + c2] -= m * J[k * n + c2];
+                b[r] -= m * b[k];
+            }
+        }
+#pragma unroll
+        for (int k = n - 1; k >= 0; k--) {
+            T sum = b[k];
+#pragma unroll
+            for (int c2 = k + 1; c2 < n; c2++) sum -= J[k * n + c2] * dX[c2];
+            dX[k] = sum / J[k * n + k];
+        }
+        if (done == 0) {
+            if (sing) {
+                bad = true;
+                done = 11;
+            } else {
+                T mx = T(0);
+#pragma unroll
+                for (int r = 0; r < n; r++) {
+                    X[r] += dX[r];
+                    mx = fmax(mx, fabs(dX[r]));
+                }
+                if (mx < tol) done = it;
+            }
+        }
+        if (!__any_sync(0xffffffffu, done == 0)) break;
+    }
+    return (bad || done == 0 || done == 11) ? -1 : done;
+}
+
+// Newton at TF nodes (Eq. system_fi) in the storage's arithmetic type, then, in FP64,
+// the fine rebuild of gamma=c populations (Eq. rescff) and on sync sub-steps the
+// coarse rebuild of all populations (Eq. rescfc).  One W-lane segment per TF node.
+template <int Q, typename S>
+__global__ void __launch_bounds__(128) k_recon(IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict__ ff,
+                                                 TimeW tw, int sync, int *status, int *max_iters)
+{
+    using L = Lat<Q>;
+    using R = typename St<S>::R;
+    constexpr int D = L::D;
+    constexpr int W = Q <= 16 ? 16 : 32;
+    const int lane = threadIdx.x & 31;
+    const int seg = (blockIdx.x * blockDim.x + threadIdx.x) / W;
+    const int i = lane % W;
+    const bool live = seg < I.nTF;
+    const int t = live ? seg : 0;
+    int c[3];
+    double wd;
+    lane_lattice<Q>(i, c[0], c[1], c[2], wd);
+    const bool pop = live && i < Q;
+    // lanes beyond Q carry nothing; a segment past the last TF node solves the rest state
+    R fhat = (!live && i < Q) ? (R)wd : R(0), gam = (!live && i < Q) ? R(1) : R(0);
+    const unsigned int gcm = I.tf_gc[t];
+    if (pop) {
+        if ((gcm >> i) & 1u) {
+            const R *hf = (const R *)I.hist_f;
+            R s = R(0);
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                if (tw.w[k] != 0.0) s += (R)tw.w[k] * hf[((long long)tw.slot[k] * Q + i) * I.nTF + t];
+            fhat = s;
+            gam = (R)I.R;
+        } else {
+            if ((I.tf_kf[t] >> i) & 1u) {
+                const int s = nb_index(F.g, I.tf_f[3 * t], I.tf_f[3 * t + 1], I.tf_f[3 * t + 2], -c[0], -c[1], -c[2]);
+                if (s >= 0) fhat = St<S>::ld(ff, (long long)i * F.g.pitch + s, wd);
+            }
+            gam = R(1);
         }
     }
-    double X[4];
-    const int it = newton_solve<Q>(fhat, Gam, X);
+    R X[4] = {R(0), R(0), R(0), R(0)};
+    const R tol = sizeof(R) == 8 ? R(1e-12) : R(2e-6);
+    const int it = newton_seg<Q, W, R>(c, i < Q ? (R)wd : R(0), fhat, gam, tol, live, X);
+    if (!live) return;
     if (it < 0) {
-        atomicOr(status, ST_NEWTON);
+        if (i == 0) atomicOr(status, ST_NEWTON);
         return;
     }
-    atomicMax(max_iters, it);
-    const int nif = F.nif;
-    for (int i = 0; i < Q; i++) {
-        const double fe = feq_one<Q>(i, X[0], X + 1);
-        const double v = ((gc >> i) & 1u) ? fe + I.R * (fhat[i] - fe) : fhat[i];
-        F.if_pop[(long long)i * nif + t] = v;
-        if (sync) Cl.if_pop[(long long)i * Cl.nif + I.tfc_base + t] = fe + (v - fe) / I.R;
+    if (i == 0) atomicMax(max_iters, it);
+    R *fpop = (R *)F.if_pop;
+    R *fmac = (R *)F.if_mac;
+    if (i < Q) {
+        // FP64 equilibrium / non-equilibrium rescaling
+        double Xd[3] = {(double)X[1], (double)X[2], (double)X[3]};
+        const double fe = feq_lane<D, double>(c, wd, (double)X[0], Xd, nullptr);
+        const double fh = (double)fhat;
+        const double v = ((gcm >> i) & 1u) ? fe + I.R * (fh - fe) : fh;
+        fpop[(long long)i * F.nif + t] = (R)v;
+        if (sync) ((R *)Cl.if_pop)[(long long)i * Cl.nif + I.tfc_base + t] = (R)(fe + (v - fe) / I.R);
     }
-    for (int a = 0; a < 4; a++) {
-        const double xv = a <= D ? X[a] : 0.0;
-        F.if_mac[(long long)a * nif + t] = xv;
-        if (sync) Cl.if_mac[(long long)a * Cl.nif + I.tfc_base + t] = xv;
+    if (i < 4) {
+        const R xv = i <= D ? X[i] : R(0);
+        fmac[(long long)i * F.nif + t] = xv;
+        if (sync) ((R *)Cl.if_mac)[(long long)i * Cl.nif + I.tfc_base + t] = xv;
     }
 }
 
@@ -157,47 +351,53 @@ template <int Q, typename S>
 __global__ void k_grad(IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict__ ff, TimeW tw, int sync)
 {
     using L = Lat<Q>;
+    using R = typename St<S>::R;
     constexpr int D = L::D;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= I.nTF) return;
-    double rho[3][2], u[3][2][3];
+    const R *fmac = (const R *)F.if_mac;
+    const R *hm = (const R *)I.hist_m;
+    R rho[3][2], u[3][2][3];
+#pragma unroll
     for (int b = 0; b < D; b++)
+#pragma unroll
         for (int s = 0; s < 2; s++) {
             const int k = t * 2 * D + 2 * b + s;
             const signed char kind = I.tf_rkind[k];
-            const long long ref = I.tf_ridx[k];
-            double r = 0.0, uu[3] = {0.0, 0.0, 0.0};
+            const int ref = I.tf_ridx[k];
+            R r = R(0), uu[3] = {R(0), R(0), R(0)};
             if (kind == RK_TF) {
-                r = F.if_mac[ref];
-                for (int a = 0; a < D; a++) uu[a] = F.if_mac[(long long)(1 + a) * F.nif + ref];
+                r = fmac[ref];
+#pragma unroll
+                for (int a = 0; a < D; a++) uu[a] = fmac[(long long)(1 + a) * F.nif + ref];
             } else if (kind == RK_RING) {
+#pragma unroll
                 for (int j = 0; j < 3; j++) {
                     if (tw.w[j] == 0.0) continue;
-                    const double *h = I.hist_m + (long long)tw.slot[j] * 4 * I.nRing;
-                    r += tw.w[j] * h[ref];
-                    for (int a = 0; a < D; a++) uu[a] += tw.w[j] * h[(long long)(1 + a) * I.nRing + ref];
+                    const R *h = hm + (long long)tw.slot[j] * 4 * I.nRing;
+                    const R wj = (R)tw.w[j];
+                    r += wj * h[ref];
+#pragma unroll
+                    for (int a = 0; a < D; a++) uu[a] += wj * h[(long long)(1 + a) * I.nRing + ref];
                 }
             } else {
-                double m[3] = {0.0, 0.0, 0.0};
-                for (int i = 0; i < Q; i++) {
-                    const long long sidx = shifted_index(F.g, ref, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
-                    const double v = sidx >= 0 ? (double)St<S>::ld(ff, (long long)i * F.g.pitch + sidx, L::w(i)) : 0.0;
-                    r += v;
-                    for (int a = 0; a < D; a++) m[a] += L::c(i, a) * v;
-                }
-                for (int a = 0; a < D; a++) uu[a] = m[a] / r;
+                const int x = ref % F.g.n[0], yz = ref / F.g.n[0];
+                pulled_moments<Q, S>(F.g, ff, x, yz % F.g.n[1], yz / F.g.n[1], r, uu);
             }
             rho[b][s] = r;
+#pragma unroll
             for (int a = 0; a < 3; a++) u[b][s][a] = uu[a];
         }
-    double Sg[6], Cg[6];
-    fd_gradients<D, double>(rho, u, 0.5, Sg, Cg);  // coarse units: neighbours one coarse cell away
+    R Sg[6], Cg[6];
+    fd_gradients<D, R>(rho, u, R(0.5), Sg, Cg);  // coarse units: neighbours one coarse cell away
+    R *fS = (R *)F.if_S, *fC = (R *)F.if_C;
+#pragma unroll
     for (int k = 0; k < 6; k++) {
-        F.if_S[(long long)k * F.nif + t] = 0.5 * Sg[k];
-        F.if_C[(long long)k * F.nif + t] = 0.5 * Cg[k];
+        fS[(long long)k * F.nif + t] = R(0.5) * Sg[k];
+        fC[(long long)k * F.nif + t] = R(0.5) * Cg[k];
         if (sync) {
-            Cl.if_S[(long long)k * Cl.nif + I.tfc_base + t] = Sg[k];
-            Cl.if_C[(long long)k * Cl.nif + I.tfc_base + t] = Cg[k];
+            ((R *)Cl.if_S)[(long long)k * Cl.nif + I.tfc_base + t] = Sg[k];
+            ((R *)Cl.if_C)[(long long)k * Cl.nif + I.tfc_base + t] = Cg[k];
         }
     }
 }
@@ -209,39 +409,48 @@ template <int Q, typename S>
 __global__ void k_ie(IfaceDev I, LevelDev F, const S *__restrict__ ff)
 {
     using L = Lat<Q>;
+    using R = typename St<S>::R;
     constexpr int D = L::D;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= I.nIE) return;
-    const long long idx = I.ie_fine[e];
+    const int x = I.ie_f[3 * e], y = I.ie_f[3 * e + 1], z = I.ie_f[3 * e + 2];
     const unsigned int kf = I.ie_kf[e];
     const int nst = I.ie_nst[e];
     const int row = I.nTF + e;  // table index of this hanging node
     const int nif = F.nif;
-    double rho = 0.0, m[3] = {0.0, 0.0, 0.0};
+    R *fpop = (R *)F.if_pop;
+    R *fmac = (R *)F.if_mac;
+    R *fS = (R *)F.if_S, *fC = (R *)F.if_C;
+    R rho = R(0), m[3] = {R(0), R(0), R(0)};
+#pragma unroll
     for (int i = 0; i < Q; i++) {
-        double v;
+        R v = R(0);
         if ((kf >> i) & 1u) {
-            const long long s = shifted_index(F.g, idx, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
-            v = s >= 0 ? (double)St<S>::ld(ff, (long long)i * F.g.pitch + s, L::w(i)) : 0.0;
+            const int s = nb_index(F.g, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
+            if (s >= 0) v = St<S>::ld(ff, (long long)i * F.g.pitch + s, L::w(i));
         } else {
-            v = 0.0;
-            for (int k = 0; k < nst; k++) v += I.ie_w[e * 16 + k] * F.if_pop[(long long)i * nif + I.ie_st[e * 16 + k]];
+            for (int k = 0; k < nst; k++) v += (R)I.ie_w[e * 16 + k] * fpop[(long long)i * nif + I.ie_st[e * 16 + k]];
         }
-        F.if_pop[(long long)i * nif + row] = v;
+        fpop[(long long)i * nif + row] = v;
         rho += v;
-        for (int a = 0; a < D; a++) m[a] += L::c(i, a) * v;
+#pragma unroll
+        for (int a = 0; a < D; a++)
+            if (L::c(i, a) != 0) m[a] += R(L::c(i, a)) * v;
     }
-    F.if_mac[row] = rho;
-    for (int a = 0; a < 3; a++) F.if_mac[(long long)(1 + a) * nif + row] = a < D ? m[a] / rho : 0.0;
+    fmac[row] = rho;
+#pragma unroll
+    for (int a = 0; a < 3; a++) fmac[(long long)(1 + a) * nif + row] = a < D ? m[a] / rho : R(0);
+#pragma unroll
     for (int k = 0; k < 6; k++) {
-        double s = 0.0, c = 0.0;
+        R s = R(0), cc = R(0);
         for (int j = 0; j < nst; j++) {
             const int tf = I.ie_st[e * 16 + j];
-            s += I.ie_w[e * 16 + j] * F.if_S[(long long)k * nif + tf];
-            c += I.ie_w[e * 16 + j] * F.if_C[(long long)k * nif + tf];
+            const R wj = (R)I.ie_w[e * 16 + j];
+            s += wj * fS[(long long)k * nif + tf];
+            cc += wj * fC[(long long)k * nif + tf];
         }
-        F.if_S[(long long)k * nif + row] = s;
-        F.if_C[(long long)k * nif + row] = c;
+        fS[(long long)k * nif + row] = s;
+        fC[(long long)k * nif + row] = cc;
     }
 }
 
@@ -282,9 +491,10 @@ __device__ __forceinline__ bool halo_macros(const LevelDev &Lv, const S *__restr
         return true;
     }
     if (htag >= 0) {
-        hr = (R)Lv.if_mac[htag];
+        const R *mac = (const R *)Lv.if_mac;
+        hr = mac[htag];
 #pragma unroll
-        for (int a = 0; a < D; a++) hu[a] = (R)Lv.if_mac[(long long)(1 + a) * Lv.nif + htag];
+        for (int a = 0; a < D; a++) hu[a] = mac[(long long)(1 + a) * Lv.nif + htag];
         return true;
     }
     return false;
@@ -299,7 +509,8 @@ __device__ __forceinline__ bool halo_macros(const LevelDev &Lv, const S *__restr
 // the box skip every class test and wrap.
 template <int Q, typename S, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
-                                                      double sigma, double spsi)
+                                                      typename St<S>::R tau, typename St<S>::R sigma,
+                                                      typename St<S>::R spsi)
 {
     using L = Lat<Q>;
     using R = typename St<S>::R;
@@ -348,8 +559,9 @@ __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__res
                 f[i] = St<S>::ld(fsrc, (long long)i * g.pitch + node_index(g, sx, sy, sz), L::w(i));
             }
         } else if (tag >= 0) {
+            const R *pop = (const R *)Lv.if_pop;
 #pragma unroll
-            for (int i = 0; i < Q; i++) f[i] = (R)Lv.if_pop[(long long)i * Lv.nif + tag];
+            for (int i = 0; i < Q; i++) f[i] = pop[(long long)i * Lv.nif + tag];
         }
     }
     if (tag == TAG_BULK) {
@@ -364,9 +576,10 @@ __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__res
 #pragma unroll
         for (int a = 0; a < D; a++) u[a] = m[a] / rho;
     } else if (tag >= 0) {
-        rho = (R)Lv.if_mac[tag];
+        const R *mac = (const R *)Lv.if_mac;
+        rho = mac[tag];
 #pragma unroll
-        for (int a = 0; a < D; a++) u[a] = (R)Lv.if_mac[(long long)(1 + a) * Lv.nif + tag];
+        for (int a = 0; a < D; a++) u[a] = mac[(long long)(1 + a) * Lv.nif + tag];
     }
     if (flag != TILE_FAST && !inside) {
         // a ragged last tile: on a periodic axis this position is the wrapped node
@@ -428,13 +641,14 @@ __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__res
             }
         fd_gradients<D, R>(nr, nu, R(0.5), Sv, Cv);
     } else {
+        const R *tS = (const R *)Lv.if_S, *tC = (const R *)Lv.if_C;
 #pragma unroll
         for (int k = 0; k < 6; k++) {
-            Sv[k] = (R)Lv.if_S[(long long)k * Lv.nif + tag];
-            Cv[k] = (R)Lv.if_C[(long long)k * Lv.nif + tag];
+            Sv[k] = tS[(long long)k * Lv.nif + tag];
+            Cv[k] = tC[(long long)k * Lv.nif + tag];
         }
     }
-    hrr_collide<Q, R>(f, rho, u, Sv, Cv, (R)Lv.tau, (R)sigma, (R)spsi);
+    hrr_collide<Q, R>(f, rho, u, Sv, Cv, tau, sigma, spsi);
 #pragma unroll
     for (int i = 0; i < Q; i++) St<S>::st(fdst, (long long)i * g.pitch + idx, f[i], L::w(i));
 }

@@ -157,7 +157,14 @@ class Hierarchy:
         L = lib()
         self.torch = torch
         self.device = torch.cuda.current_device()
-        self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
+        cur = stream if stream is not None else torch.cuda.current_stream()
+        if cur.cuda_stream == 0:
+            # the legacy default stream cannot be captured into CUDA graphs: the handle
+            # gets a stream of its own, ordered against the caller's stream at every call
+            # that takes device tensors
+            cur = torch.cuda.Stream()
+        self._stream_obj = cur
+        self.stream = cur
         d = make_desc(desc, use_graphs)
         self._alloc = None
         if torch_alloc:
@@ -175,6 +182,14 @@ class Hierarchy:
         self.levels = [self.query_level(l) for l in range(self.n_levels)]
 
     # -------------------------------------------------------------- helpers
+    def _enter(self, dev):
+        if dev:
+            self.stream.wait_stream(self.torch.cuda.current_stream())
+
+    def _leave(self, dev):
+        if dev:
+            self.torch.cuda.current_stream().wait_stream(self.stream)
+
     def _check(self, rc):
         if rc != LBM_OK:
             raise LbmError(rc, lib().lbm_last_error(self._h).decode())
@@ -213,7 +228,9 @@ class Hierarchy:
             u = np.ascontiguousarray(u, dtype=np.float64).reshape(self.D, N)
         pr, dev = _ptr(rho)
         pu, _ = _ptr(u)
+        self._enter(dev)
         self._check(lib().lbm_init_fields(self._h, l, pr, pu, dev))
+        self._leave(dev)
 
     def advance(self, n):
         self._check(lib().lbm_advance(self._h, int(n)))
@@ -228,7 +245,9 @@ class Hierarchy:
             rho, u = out
         pr, dev = _ptr(rho)
         pu, _ = _ptr(u)
+        self._enter(dev)
         self._check(lib().lbm_get_macros(self._h, l, pr, pu, dev))
+        self._leave(dev)
         return rho, u
 
     def get_pops(self, l):
