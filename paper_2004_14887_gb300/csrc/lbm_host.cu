@@ -668,13 +668,14 @@ struct Sched {
         Level &v = h->lev[l];
         const void *fA = v.f[k & 1];
         void *fB = v.f[(k + 1) & 1];
-        const int B = 32;  // one warp per block: O(surface) work spread over many SMs
+        // interface kernels: one 16- (D2Q9) or 32-lane (D3Q19) segment per node, 128 threads per block
+        constexpr int SEG = 128 / (Q <= 16 ? 16 : 32);
         LevelDev dv = level_dev(h, l);
         if (l + 1 < h->nl) {
             const IfaceDev &I = h->ifc[l + 1].dev;
             const int n = I.nTF + I.nRing;
             if (n > 0) {
-                k_hist<Q, S><<<(n + B - 1) / B, B, 0, h->stream>>>(I, dv.g, (const S *)fA, (int)((k + 1) % 3), 0);
+                k_hist<Q, S><<<(n + SEG - 1) / SEG, 128, 0, h->stream>>>(I, dv.g, (const S *)fA, (int)((k + 1) % 3), 0);
                 h->launch_counter++;
             }
         }
@@ -683,8 +684,7 @@ struct Sched {
             tw = weights(phase, kp);
             const IfaceDev &I = h->ifc[l].dev;
             if (I.nTF > 0) {
-                constexpr int per_block = 128 / (Q <= 16 ? 16 : 32);
-                k_recon<Q, S><<<(I.nTF + per_block - 1) / per_block, 128, 0, h->stream>>>(
+                k_recon<Q, S><<<(I.nTF + SEG - 1) / SEG, 128, 0, h->stream>>>(
                     I, dv, level_dev(h, l - 1), (const S *)fA, tw, phase, h->d_status, h->d_maxit);
                 h->launch_counter++;
             }
@@ -696,12 +696,12 @@ struct Sched {
         if (l > 0) {
             const IfaceDev &I = h->ifc[l].dev;
             if (I.nTF > 0) {
-                k_grad<Q, S><<<(I.nTF + B - 1) / B, B, 0, h->stream>>>(I, dv, level_dev(h, l - 1), (const S *)fA, tw,
-                                                                      phase);
+                k_grad<Q, S><<<(I.nTF + SEG - 1) / SEG, 128, 0, h->stream>>>(I, dv, level_dev(h, l - 1), (const S *)fA,
+                                                                            tw, phase);
                 h->launch_counter++;
             }
             if (I.nIE > 0) {
-                k_ie<Q, S><<<(I.nIE + B - 1) / B, B, 0, h->stream>>>(I, dv, (const S *)fA);
+                k_ie<Q, S><<<(I.nIE + SEG - 1) / SEG, 128, 0, h->stream>>>(I, dv, (const S *)fA);
                 h->launch_counter++;
             }
         }
@@ -720,7 +720,8 @@ struct Sched {
         if (l + 1 < h->nl) {
             const IfaceDev &I = h->ifc[l + 1].dev;
             const int n = I.nTF + I.nRing;
-            if (n > 0) k_hist<Q, S><<<(n + 31) / 32, 32, 0, h->stream>>>(I, dv.g, (const S *)v.f[0], 0, 1);
+            constexpr int SEG = 128 / (Q <= 16 ? 16 : 32);
+            if (n > 0) k_hist<Q, S><<<(n + SEG - 1) / SEG, 128, 0, h->stream>>>(I, dv.g, (const S *)v.f[0], 0, 1);
         }
         return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
     }

@@ -75,56 +75,6 @@ __device__ __forceinline__ void pulled_moments(const LevelGeo &g, const S *__res
     for (int a = 0; a < 3; a++) u[a] = a < D ? m[a] / r : R(0);
 }
 
-// ------------------------------------------------------------------ history push
-// post-stream coarse populations at TF nodes (coarse-known ones) and post-stream
-// macros at ring nodes, for the child level's Eq. (TempInt)
-template <int Q, typename S>
-__global__ void k_hist(IfaceDev I, LevelGeo gc, const S *__restrict__ fc, int slot, int seed)
-{
-    using L = Lat<Q>;
-    using R = typename St<S>::R;
-    constexpr int D = L::D;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    R *hf = (R *)I.hist_f;
-    R *hm = (R *)I.hist_m;
-    if (t < I.nTF) {
-        const int x = I.tf_c[3 * t], y = I.tf_c[3 * t + 1], z = I.tf_c[3 * t + 2];
-        const unsigned int kc = I.tf_kc[t];
-#pragma unroll
-        for (int i = 0; i < Q; i++) {
-            R v = R(0);
-            // seed: slot 0 holds the initial state itself; otherwise the post-stream value
-            const int s = seed ? box_index(gc, x, y, z)
-                               : (((kc >> i) & 1u) ? nb_index(gc, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2)) : -1);
-            if (s >= 0) v = St<S>::ld(fc, (long long)i * gc.pitch + s, L::w(i));
-            hf[((long long)slot * Q + i) * I.nTF + t] = v;
-        }
-    } else if (t < I.nTF + I.nRing) {
-        const int r = t - I.nTF;
-        const int x = I.ring_c[3 * r], y = I.ring_c[3 * r + 1], z = I.ring_c[3 * r + 2];
-        R rho, u[3];
-        if (seed) {
-            R m[3] = {R(0), R(0), R(0)};
-            rho = R(0);
-            const int s = box_index(gc, x, y, z);
-#pragma unroll
-            for (int i = 0; i < Q; i++) {
-                const R v = St<S>::ld(fc, (long long)i * gc.pitch + s, L::w(i));
-                rho += v;
-#pragma unroll
-                for (int a = 0; a < D; a++)
-                    if (L::c(i, a) != 0) m[a] += R(L::c(i, a)) * v;
-            }
-            for (int a = 0; a < 3; a++) u[a] = a < D ? m[a] / rho : R(0);
-        } else {
-            pulled_moments<Q, S>(gc, fc, x, y, z, rho, u);
-        }
-        R *h = hm + (long long)slot * 4 * I.nRing;
-        h[r] = rho;
-        for (int a = 0; a < 3; a++) h[(long long)(1 + a) * I.nRing + r] = u[a];
-    }
-}
-
 // ------------------------------------------------------------------ TF reconstruction
 // segmented warp reduction over the W lanes that hold one TF node's populations
 template <int W, typename T>
@@ -343,18 +293,71 @@ __global__ void __launch_bounds__(128) k_recon(IfaceDev I, LevelDev F, LevelDev 
     }
 }
 
-// ------------------------------------------------------------------ TF gradients
-// Sec. 3.3: centred differences over the coarse stencil (fine nodes two fine cells
-// inward, TF neighbours along the interface with their X, coarse ring nodes outward,
-// time-interpolated on async sub-steps), rescaled by 1/2 for the fine level.
+// ------------------------------------------------------------------ history push
+// post-stream coarse populations at TF nodes (coarse-known ones) and post-stream
+// macros at ring nodes, for the child level's Eq. (TempInt).  One W-lane segment
+// per node, lane i handles population i (TF segments first, then ring segments).
 template <int Q, typename S>
-__global__ void k_grad(IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict__ ff, TimeW tw, int sync)
+__global__ void __launch_bounds__(128) k_hist(IfaceDev I, LevelGeo gc, const S *__restrict__ fc, int slot, int seed)
 {
     using L = Lat<Q>;
     using R = typename St<S>::R;
     constexpr int D = L::D;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= I.nTF) return;
+    constexpr int W = Q <= 16 ? 16 : 32;
+    const int seg = (blockIdx.x * blockDim.x + threadIdx.x) / W;
+    const int i = threadIdx.x % W;
+    int c[3];
+    double wd;
+    lane_lattice<Q>(i, c[0], c[1], c[2], wd);
+    const bool is_tf = seg < I.nTF;
+    const int r = seg - I.nTF;
+    const bool live_ring = !is_tf && r < I.nRing;
+    if (is_tf && i < Q) {
+        const int t = seg;
+        const int x = I.tf_c[3 * t], y = I.tf_c[3 * t + 1], z = I.tf_c[3 * t + 2];
+        // seed: slot 0 holds the initial state itself; otherwise the post-stream value
+        const int s = seed ? box_index(gc, x, y, z)
+                           : (((I.tf_kc[t] >> i) & 1u) ? nb_index(gc, x, y, z, -c[0], -c[1], -c[2]) : -1);
+        ((R *)I.hist_f)[((long long)slot * Q + i) * I.nTF + t] =
+            s >= 0 ? St<S>::ld(fc, (long long)i * gc.pitch + s, wd) : R(0);
+    }
+    R v = R(0);
+    if (live_ring && i < Q) {
+        const int x = I.ring_c[3 * r], y = I.ring_c[3 * r + 1], z = I.ring_c[3 * r + 2];
+        const int s = seed ? box_index(gc, x, y, z) : nb_index(gc, x, y, z, -c[0], -c[1], -c[2]);
+        if (s >= 0) v = St<S>::ld(fc, (long long)i * gc.pitch + s, wd);
+    }
+    const R rho = seg_sum<W>(v);
+    R m[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int a = 0; a < D; a++) m[a] = seg_sum<W>(R(c[a]) * v);
+    if (live_ring && i < 4) {
+        R *h = (R *)I.hist_m + (long long)slot * 4 * I.nRing;
+        h[(long long)i * I.nRing + r] = i == 0 ? rho : (i <= D ? m[i - 1] / rho : R(0));
+    }
+}
+
+// ------------------------------------------------------------------ TF gradients
+// Sec. 3.3: centred differences over the coarse stencil (fine nodes two fine cells
+// inward, TF neighbours along the interface with their X, coarse ring nodes outward,
+// time-interpolated on async sub-steps), rescaled by 1/2 for the fine level.  One
+// W-lane segment per TF node: the lanes pull the populations of fine neighbours in
+// parallel; every lane then holds the stencil and lanes 0..11 write S and C.
+template <int Q, typename S>
+__global__ void __launch_bounds__(128) k_grad(IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict__ ff,
+                                                TimeW tw, int sync)
+{
+    using L = Lat<Q>;
+    using R = typename St<S>::R;
+    constexpr int D = L::D;
+    constexpr int W = Q <= 16 ? 16 : 32;
+    const int seg = (blockIdx.x * blockDim.x + threadIdx.x) / W;
+    const int i = threadIdx.x % W;
+    const bool live = seg < I.nTF;
+    const int t = live ? seg : 0;
+    int c[3];
+    double wd;
+    lane_lattice<Q>(i, c[0], c[1], c[2], wd);
     const R *fmac = (const R *)F.if_mac;
     const R *hm = (const R *)I.hist_m;
     R rho[3][2], u[3][2][3];
@@ -365,12 +368,25 @@ __global__ void k_grad(IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict_
             const int k = t * 2 * D + 2 * b + s;
             const signed char kind = I.tf_rkind[k];
             const int ref = I.tf_ridx[k];
-            R r = R(0), uu[3] = {R(0), R(0), R(0)};
-            if (kind == RK_TF) {
+            // fine neighbour: lane i pulls its population i (zero for other kinds)
+            R v = R(0);
+            if (live && kind == RK_FINE && i < Q) {
+                const int x = ref % F.g.n[0], yz = ref / F.g.n[0];
+                const int src = nb_index(F.g, x, yz % F.g.n[1], yz / F.g.n[1], -c[0], -c[1], -c[2]);
+                if (src >= 0) v = St<S>::ld(ff, (long long)i * F.g.pitch + src, wd);
+            }
+            R r = seg_sum<W>(v), uu[3] = {R(0), R(0), R(0)};
+#pragma unroll
+            for (int a = 0; a < D; a++) uu[a] = seg_sum<W>(R(c[a]) * v);
+            if (kind == RK_FINE) {
+#pragma unroll
+                for (int a = 0; a < D; a++) uu[a] /= r;
+            } else if (kind == RK_TF) {
                 r = fmac[ref];
 #pragma unroll
                 for (int a = 0; a < D; a++) uu[a] = fmac[(long long)(1 + a) * F.nif + ref];
-            } else if (kind == RK_RING) {
+            } else {
+                r = R(0);
 #pragma unroll
                 for (int j = 0; j < 3; j++) {
                     if (tw.w[j] == 0.0) continue;
@@ -380,78 +396,68 @@ __global__ void k_grad(IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict_
 #pragma unroll
                     for (int a = 0; a < D; a++) uu[a] += wj * h[(long long)(1 + a) * I.nRing + ref];
                 }
-            } else {
-                const int x = ref % F.g.n[0], yz = ref / F.g.n[0];
-                pulled_moments<Q, S>(F.g, ff, x, yz % F.g.n[1], yz / F.g.n[1], r, uu);
             }
             rho[b][s] = r;
 #pragma unroll
-            for (int a = 0; a < 3; a++) u[b][s][a] = uu[a];
+            for (int a = 0; a < 3; a++) u[b][s][a] = a < D ? uu[a] : R(0);
         }
+    if (!live) return;
     R Sg[6], Cg[6];
     fd_gradients<D, R>(rho, u, R(0.5), Sg, Cg);  // coarse units: neighbours one coarse cell away
-    R *fS = (R *)F.if_S, *fC = (R *)F.if_C;
-#pragma unroll
-    for (int k = 0; k < 6; k++) {
-        fS[(long long)k * F.nif + t] = R(0.5) * Sg[k];
-        fC[(long long)k * F.nif + t] = R(0.5) * Cg[k];
-        if (sync) {
-            ((R *)Cl.if_S)[(long long)k * Cl.nif + I.tfc_base + t] = Sg[k];
-            ((R *)Cl.if_C)[(long long)k * Cl.nif + I.tfc_base + t] = Cg[k];
-        }
+    if (i < 12) {
+        const int k = i % 6;
+        R *dstF = (R *)(i < 6 ? F.if_S : F.if_C);
+        const R val = i < 6 ? Sg[k] : Cg[k];
+        dstF[(long long)k * F.nif + t] = R(0.5) * val;
+        if (sync) ((R *)(i < 6 ? Cl.if_S : Cl.if_C))[(long long)k * Cl.nif + I.tfc_base + t] = val;
     }
 }
 
 // ------------------------------------------------------------------ hanging nodes
 // 4-point 1-D Lagrange along the interface (tensor order over odd axes, one-sided
-// next to corners) of missing populations, S and C; macros are the moments.
+// next to corners) of missing populations, S and C; macros are the moments.  One
+// W-lane segment per hanging node: lane i completes population i, lanes 0..11
+// interpolate the S and C components.
 template <int Q, typename S>
-__global__ void k_ie(IfaceDev I, LevelDev F, const S *__restrict__ ff)
+__global__ void __launch_bounds__(128) k_ie(IfaceDev I, LevelDev F, const S *__restrict__ ff)
 {
     using L = Lat<Q>;
     using R = typename St<S>::R;
     constexpr int D = L::D;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= I.nIE) return;
-    const int x = I.ie_f[3 * e], y = I.ie_f[3 * e + 1], z = I.ie_f[3 * e + 2];
-    const unsigned int kf = I.ie_kf[e];
-    const int nst = I.ie_nst[e];
-    const int row = I.nTF + e;  // table index of this hanging node
+    constexpr int W = Q <= 16 ? 16 : 32;
+    const int seg = (blockIdx.x * blockDim.x + threadIdx.x) / W;
+    const int i = threadIdx.x % W;
+    const bool live = seg < I.nIE;
+    const int e = live ? seg : 0;
+    int c[3];
+    double wd;
+    lane_lattice<Q>(i, c[0], c[1], c[2], wd);
     const int nif = F.nif;
+    const int row = I.nTF + e;  // table index of this hanging node
     R *fpop = (R *)F.if_pop;
-    R *fmac = (R *)F.if_mac;
-    R *fS = (R *)F.if_S, *fC = (R *)F.if_C;
-    R rho = R(0), m[3] = {R(0), R(0), R(0)};
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        R v = R(0);
-        if ((kf >> i) & 1u) {
-            const int s = nb_index(F.g, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
-            if (s >= 0) v = St<S>::ld(ff, (long long)i * F.g.pitch + s, L::w(i));
+    const int nst = I.ie_nst[e];
+    R v = R(0);
+    if (live && i < Q) {
+        if ((I.ie_kf[e] >> i) & 1u) {
+            const int s = nb_index(F.g, I.ie_f[3 * e], I.ie_f[3 * e + 1], I.ie_f[3 * e + 2], -c[0], -c[1], -c[2]);
+            if (s >= 0) v = St<S>::ld(ff, (long long)i * F.g.pitch + s, wd);
         } else {
             for (int k = 0; k < nst; k++) v += (R)I.ie_w[e * 16 + k] * fpop[(long long)i * nif + I.ie_st[e * 16 + k]];
         }
         fpop[(long long)i * nif + row] = v;
-        rho += v;
-#pragma unroll
-        for (int a = 0; a < D; a++)
-            if (L::c(i, a) != 0) m[a] += R(L::c(i, a)) * v;
     }
-    fmac[row] = rho;
-#pragma unroll
-    for (int a = 0; a < 3; a++) fmac[(long long)(1 + a) * nif + row] = a < D ? m[a] / rho : R(0);
-#pragma unroll
-    for (int k = 0; k < 6; k++) {
-        R s = R(0), cc = R(0);
-        for (int j = 0; j < nst; j++) {
-            const int tf = I.ie_st[e * 16 + j];
-            const R wj = (R)I.ie_w[e * 16 + j];
-            s += wj * fS[(long long)k * nif + tf];
-            cc += wj * fC[(long long)k * nif + tf];
-        }
-        fS[(long long)k * nif + row] = s;
-        fC[(long long)k * nif + row] = cc;
+    if (live && i < 12) {
+        const int k = i % 6;
+        R *tab = (R *)(i < 6 ? F.if_S : F.if_C);
+        R acc = R(0);
+        for (int j = 0; j < nst; j++) acc += (R)I.ie_w[e * 16 + j] * tab[(long long)k * nif + I.ie_st[e * 16 + j]];
+        tab[(long long)k * nif + row] = acc;
     }
+    const R rho = seg_sum<W>(v);
+    R m[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int a = 0; a < D; a++) m[a] = seg_sum<W>(R(c[a]) * v);
+    if (live && i < 4) ((R *)F.if_mac)[(long long)i * nif + row] = i == 0 ? rho : (i <= D ? m[i - 1] / rho : R(0));
 }
 
 // rho, u of the node at box coordinates (xx, yy, zz) for the shared-memory halo:
@@ -542,10 +548,55 @@ __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__res
 
     if (flag == TILE_FAST) {
         tag = TAG_BULK;
+        if constexpr (D == 2) {
+            // 2-D tiles have fewer halo nodes than threads: thread tid < NB also owns
+            // border position tid, and its halo loads go out with its own loads
+            constexpr int NB = H - NT;
+            static_assert(NB <= NT, "one halo node per thread at most");
+            int hb = -1;
+            long long hidx = 0;
+            if (tid < NB) {
+                int hx, hy;
+                if (tid < HX) {
+                    hx = tid;
+                    hy = 0;
+                } else if (tid < 2 * HX) {
+                    hx = tid - HX;
+                    hy = HY - 1;
+                } else {
+                    const int b = tid - 2 * HX;
+                    hy = 1 + (b >> 1);
+                    hx = (b & 1) ? HX - 1 : 0;
+                }
+                hb = hx + HX * hy;
+                hidx = (long long)(X0 + hx - 1) + (long long)g.n[0] * (Y0 + hy - 1);
+            }
+            R fh[Q];
 #pragma unroll
-        for (int i = 0; i < Q; i++) {
-            const long long off = (long long)L::c(i, 0) + (long long)g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
-            f[i] = St<S>::ld(fsrc, (long long)i * g.pitch + idx - off, L::w(i));
+            for (int i = 0; i < Q; i++) {
+                const long long off = (long long)L::c(i, 0) + (long long)g.n[0] * L::c(i, 1);
+                f[i] = St<S>::ld(fsrc, (long long)i * g.pitch + idx - off, L::w(i));
+                fh[i] = hb >= 0 ? St<S>::ld(fsrc, (long long)i * g.pitch + hidx - off, L::w(i)) : R(0);
+            }
+            if (hb >= 0) {
+                R hr = R(0), m[3] = {R(0), R(0), R(0)};
+#pragma unroll
+                for (int i = 0; i < Q; i++) {
+                    hr += fh[i];
+#pragma unroll
+                    for (int a = 0; a < D; a++)
+                        if (L::c(i, a) != 0) m[a] += R(L::c(i, a)) * fh[i];
+                }
+                s_rho[hb] = hr;
+#pragma unroll
+                for (int a = 0; a < D; a++) s_u[a][hb] = m[a] / hr;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; i++) {
+                const long long off = (long long)L::c(i, 0) + (long long)g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
+                f[i] = St<S>::ld(fsrc, (long long)i * g.pitch + idx - off, L::w(i));
+            }
         }
     } else if (inside) {
         tag = Lv.tag[idx];
@@ -593,8 +644,8 @@ __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__res
 #pragma unroll
     for (int a = 0; a < D; a++) s_u[a][hself] = u[a];
 
-    // halo ring
-    for (int h = tid; h < H; h += NT) {
+    // halo ring (2-D fast tiles loaded it above)
+    for (int h = tid; h < H && !(D == 2 && flag == TILE_FAST); h += NT) {
         const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
         const bool border = hx == 0 || hx == HX - 1 || hy == 0 || hy == HY - 1 || (D == 3 && (hz == 0 || hz == HZ - 1));
         if (!border) continue;
