@@ -212,11 +212,11 @@ __device__ __forceinline__ void fd_gradients(const R (&rho)[3][2], const R (&u)[
 // H-RR collision of one node, Eq. (LBMscheme_reg), in the compact Hermite form
 //   f_i = w_i [ rho (1 + c.u/cs2) + H2_i:B/(2cs2^2) + sum_{a!=b} H3_i,aab T_ab/(2cs2^3) ]
 // with B = rho uu + (1-1/tau) a1 + (s/2) C and T_ab = rho u_a^2 u_b + (1-1/tau) a1_aab,
-// which is f0 + (1-1/tau) f1_reg + psi/2 term by term.  a1 follows Eq. (a12_HRR):
+// which is f0 + (1-1/tau) f1_reg + psi/2 term by term (om = 1 - 1/tau).  a1 follows Eq. (a12_HRR):
 // a1^PR = sum_i H2_i (f_i - f0_i + psi_i/2) = Pi - cs2 sum(f) I - rho uu + (s/2) C
 // (Hermite orthogonality), a1^FD = -2 tau rho cs2 S.
 template <int Q, typename R>
-__device__ __forceinline__ void hrr_collide(R (&f)[Q], R rho, const R *u, const R *S, const R *C, R tau,
+__device__ __forceinline__ void hrr_collide(R (&f)[Q], R rho, const R *u, const R *S, const R *C, R tau, R om,
                                             R sigma, R spsi)
 {
     using L = Lat<Q>;
@@ -233,7 +233,6 @@ __device__ __forceinline__ void hrr_collide(R (&f)[Q], R rho, const R *u, const 
             for (int b = a; b < D; b++)
                 if (L::c(i, a) * L::c(i, b) != 0) Pi[sym_index(a, b)] += R(L::c(i, a) * L::c(i, b)) * f[i];
     }
-    const R om = R(1) - R(1) / tau;
     const R kfd = R(-2) * tau * rho * cs2;
     R B[6], A[6];
 #pragma unroll

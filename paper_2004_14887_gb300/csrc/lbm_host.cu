@@ -613,7 +613,7 @@ struct Sched {
     static void bulk(lbm_h h, int l, const void *src, void *dst)
     {
         const Level &v = h->lev[l];
-        const int nt = v.tiles[0] * v.tiles[1] * v.tiles[2];
+        const dim3 nt(v.tiles[0], v.tiles[1], v.tiles[2]);
         const double spsi = (double)h->d.psi_sign;
         int ev = -1;
         if (h->timing) {
@@ -626,13 +626,13 @@ struct Sched {
             cudaEventRecord(h->ev_pool[ev], h->stream);
         }
         using R = typename St<S>::R;
-        const R tau = (R)v.tau, sig = (R)h->d.sigma, sps = (R)spsi;
+        const R tau = (R)v.tau, om = (R)(1.0 - 1.0 / v.tau), sig = (R)h->d.sigma, sps = (R)spsi;
         if constexpr (Lat<Q>::D == 2)
             k_bulk<Q, S, T2X, T2Y, 1><<<nt, T2X * T2Y, 0, h->stream>>>(level_dev(h, l), (const S *)src, (S *)dst, tau,
-                                                                      sig, sps);
+                                                                      om, sig, sps);
         else
             k_bulk<Q, S, T3X, T3Y, T3Z><<<nt, T3X * T3Y * T3Z, 0, h->stream>>>(level_dev(h, l), (const S *)src,
-                                                                              (S *)dst, tau, sig, sps);
+                                                                              (S *)dst, tau, om, sig, sps);
         h->launch_counter++;
         if (h->timing) {
             cudaEventRecord(h->ev_pool[ev + 1], h->stream);

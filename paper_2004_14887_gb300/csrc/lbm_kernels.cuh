@@ -515,8 +515,8 @@ __device__ __forceinline__ bool halo_macros(const LevelDev &Lv, const S *__restr
 // the box skip every class test and wrap.
 template <int Q, typename S, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
-                                                      typename St<S>::R tau, typename St<S>::R sigma,
-                                                      typename St<S>::R spsi)
+                                                      typename St<S>::R tau, typename St<S>::R om,
+                                                      typename St<S>::R sigma, typename St<S>::R spsi)
 {
     using L = Lat<Q>;
     using R = typename St<S>::R;
@@ -528,22 +528,20 @@ __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__res
     __shared__ R s_u[D][H];
 
     const LevelGeo &g = Lv.g;
-    const int bx = blockIdx.x % Lv.tiles[0];
-    const int by = (blockIdx.x / Lv.tiles[0]) % Lv.tiles[1];
-    const int bz = blockIdx.x / (Lv.tiles[0] * Lv.tiles[1]);
-    const unsigned char flag = Lv.tile_flag[blockIdx.x];
+    const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
+    const unsigned char flag = Lv.tile_flag[bx + Lv.tiles[0] * (by + Lv.tiles[1] * bz)];
     if (flag == TILE_SKIP) return;
     const int X0 = bx * TX, Y0 = by * TY, Z0 = bz * (D == 3 ? TZ : 1);
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = (tid / TX) % TY, tz = tid / (TX * TY);
     const int x = X0 + tx, y = Y0 + ty, z = Z0 + (D == 3 ? tz : 0);
-    const long long n01 = (long long)g.n[0] * g.n[1];
+    const int n01 = g.n[0] * g.n[1];  // boxes hold fewer than 2^31 nodes
 
     R f[Q];
     R rho = R(0), u[3] = {R(0), R(0), R(0)};
     int tag = TAG_HOLE;
     const bool inside = x < g.n[0] && y < g.n[1] && z < g.n[2];
-    const long long idx = (long long)x + (long long)g.n[0] * y + n01 * z;
+    const int idx = x + g.n[0] * y + n01 * z;
     const int hself = (tx + 1) + HX * ((ty + 1) + HY * (D == 3 ? tz + 1 : 0));
 
     if (flag == TILE_FAST) {
@@ -554,7 +552,7 @@ __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__res
             constexpr int NB = H - NT;
             static_assert(NB <= NT, "one halo node per thread at most");
             int hb = -1;
-            long long hidx = 0;
+            int hidx = 0;
             if (tid < NB) {
                 int hx, hy;
                 if (tid < HX) {
@@ -569,14 +567,15 @@ __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__res
                     hx = (b & 1) ? HX - 1 : 0;
                 }
                 hb = hx + HX * hy;
-                hidx = (long long)(X0 + hx - 1) + (long long)g.n[0] * (Y0 + hy - 1);
+                hidx = (X0 + hx - 1) + g.n[0] * (Y0 + hy - 1);
             }
             R fh[Q];
 #pragma unroll
             for (int i = 0; i < Q; i++) {
-                const long long off = (long long)L::c(i, 0) + (long long)g.n[0] * L::c(i, 1);
-                f[i] = St<S>::ld(fsrc, (long long)i * g.pitch + idx - off, L::w(i));
-                fh[i] = hb >= 0 ? St<S>::ld(fsrc, (long long)i * g.pitch + hidx - off, L::w(i)) : R(0);
+                const S *pi = fsrc + (long long)i * g.pitch;  // population plane
+                const int off = L::c(i, 0) + g.n[0] * L::c(i, 1);
+                f[i] = St<S>::ld(pi, idx - off, L::w(i));
+                fh[i] = hb >= 0 ? St<S>::ld(pi, hidx - off, L::w(i)) : R(0);
             }
             if (hb >= 0) {
                 R hr = R(0), m[3] = {R(0), R(0), R(0)};
@@ -588,14 +587,15 @@ __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__res
                         if (L::c(i, a) != 0) m[a] += R(L::c(i, a)) * fh[i];
                 }
                 s_rho[hb] = hr;
+                const R inv = R(1) / hr;
 #pragma unroll
-                for (int a = 0; a < D; a++) s_u[a][hb] = m[a] / hr;
+                for (int a = 0; a < D; a++) s_u[a][hb] = m[a] * inv;
             }
         } else {
 #pragma unroll
             for (int i = 0; i < Q; i++) {
-                const long long off = (long long)L::c(i, 0) + (long long)g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
-                f[i] = St<S>::ld(fsrc, (long long)i * g.pitch + idx - off, L::w(i));
+                const int off = L::c(i, 0) + g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
+                f[i] = St<S>::ld(fsrc + (long long)i * g.pitch, idx - off, L::w(i));
             }
         }
     } else if (inside) {
@@ -624,8 +624,9 @@ __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__res
             for (int a = 0; a < D; a++)
                 if (L::c(i, a) != 0) m[a] += R(L::c(i, a)) * f[i];
         }
+        const R inv = R(1) / rho;
 #pragma unroll
-        for (int a = 0; a < D; a++) u[a] = m[a] / rho;
+        for (int a = 0; a < D; a++) u[a] = m[a] * inv;
     } else if (tag >= 0) {
         const R *mac = (const R *)Lv.if_mac;
         rho = mac[tag];
@@ -652,13 +653,13 @@ __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__res
         int xx = X0 + hx - 1, yy = Y0 + hy - 1, zz = Z0 + (D == 3 ? hz - 1 : 0);
         R hr = R(1), hu[3] = {R(0), R(0), R(0)};
         if (flag == TILE_FAST) {
-            const long long hidx = (long long)xx + (long long)g.n[0] * yy + n01 * zz;
+            const int hidx = xx + g.n[0] * yy + n01 * zz;
             R m[3] = {R(0), R(0), R(0)};
             hr = R(0);
 #pragma unroll
             for (int i = 0; i < Q; i++) {
-                const long long off = (long long)L::c(i, 0) + (long long)g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
-                const R v = St<S>::ld(fsrc, (long long)i * g.pitch + hidx - off, L::w(i));
+                const int off = L::c(i, 0) + g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
+                const R v = St<S>::ld(fsrc + (long long)i * g.pitch, hidx - off, L::w(i));
                 hr += v;
 #pragma unroll
                 for (int a = 0; a < D; a++)
@@ -699,9 +700,9 @@ __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__res
             Cv[k] = tC[(long long)k * Lv.nif + tag];
         }
     }
-    hrr_collide<Q, R>(f, rho, u, Sv, Cv, tau, sigma, spsi);
+    hrr_collide<Q, R>(f, rho, u, Sv, Cv, tau, om, sigma, spsi);
 #pragma unroll
-    for (int i = 0; i < Q; i++) St<S>::st(fdst, (long long)i * g.pitch + idx, f[i], L::w(i));
+    for (int i = 0; i < Q; i++) St<S>::st(fdst + (long long)i * g.pitch, idx, f[i], L::w(i));
 }
 
 // ------------------------------------------------------------------ utilities
