@@ -140,6 +140,27 @@ LBM_API int lbm_get_pops(lbm_h h, int level, double *f_out, int on_device);
  * LBM_ERR_DIVERGED if a NaN or Inf was met. */
 LBM_API int lbm_reduce(lbm_h h, int level, double out[4]);
 
+/* Allocation-free variant of lbm_reduce (the paper has no counterpart; this is a
+ * library service).  For callers that may not allocate device memory once they are
+ * running -- for instance a host process whose device heap is entirely handed to
+ * its own pool allocator, or a fixed-latency control loop that forbids cudaMalloc
+ * after start-up.  The per-block partial sums live in a static device array of
+ * LBM_STATIC_REDUCE_PARTIALS x 4 doubles (+4 for the result, about 128 KB) that
+ * every GPU loading the library holds until the process exits; the call itself
+ * calls no cudaMalloc, cudaFree or allocating library routine.
+ *   - Same inputs, output and weights as lbm_reduce; out is a host buffer of 4 doubles.
+ *   - Levels with more than LBM_STATIC_REDUCE_PARTIALS x 2048 box nodes are rejected
+ *     with LBM_ERR_ARG and a message naming the limit.
+ *   - The handle's device must be the current device.  The first call on a device
+ *     looks up the array's device address (cudaGetSymbolAddress) and caches it; make
+ *     that first call before any stream capture on that device.
+ *   - All calls share the one array: calls whose work overlaps on the GPU (two
+ *     streams, or two host threads) race and may return wrong sums.  Each call
+ *     overwrites every partial it reads, so nothing has to be cleared between calls.
+ *   - Synchronises the handle's stream; returns LBM_ERR_DIVERGED on NaN or Inf. */
+#define LBM_STATIC_REDUCE_PARTIALS 4096
+LBM_API int lbm_reduce_static(lbm_h h, int level, double out[4]);
+
 /* Device status word accumulated by the kernels since the last call (cleared on read):
  * returns LBM_OK, LBM_ERR_NEWTON or LBM_ERR_DIVERGED.  Synchronises the stream. */
 LBM_API int lbm_check_status(lbm_h h);

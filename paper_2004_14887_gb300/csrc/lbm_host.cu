@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1055,3 +1056,77 @@ void lbm_destroy(lbm_h h)
 }
 
 }  // extern "C"
+
+// ================================================================== allocation-free reduction
+// The level reduction above keeps its per-block partial sums in a buffer the handle
+// allocated at creation.  This variant keeps them in a fixed array of static device
+// memory instead, so the call itself never allocates: every GPU that loads the library
+// holds the array (LBM_STATIC_REDUCE_PARTIALS x 4 doubles + 4, about 128 KB) until the
+// process exits.  Host code cannot use the array's name as a device address; its
+// address is looked up once per device with cudaGetSymbolAddress.
+namespace {
+constexpr int kStaticPartials = LBM_STATIC_REDUCE_PARTIALS;
+constexpr int kStaticNodesPerBlock = 256 * 8;
+static __device__ __align__(256) double g_static_reduce[kStaticPartials * 4 + 4];
+std::mutex g_static_mtx;
+double *g_static_addr[256] = {nullptr};
+}  // namespace
+
+extern "C" int lbm_reduce_static(lbm_h h, int level, double out[4])
+{
+    if (!check_level(h, level)) return LBM_ERR_ARG;
+    if (!out) return fail(h, LBM_ERR_ARG, "out is NULL");
+    const Level &v = h->lev[level];
+    const long long blocks = (v.N + kStaticNodesPerBlock - 1) / kStaticNodesPerBlock;
+    if (blocks > kStaticPartials)
+        return fail(h, LBM_ERR_ARG,
+                    "level %d has %lld box nodes; the static-scratch reduction handles at most %lld "
+                    "(use lbm_reduce)", level, v.N, (long long)kStaticPartials * kStaticNodesPerBlock);
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return fail(h, LBM_ERR_ARG, "device ordinal %d out of range", dev);
+    double *scratch;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mtx);
+        if (!g_static_addr[dev]) {
+            void *p = nullptr;
+            CK(cudaGetSymbolAddress(&p, g_static_reduce));
+            g_static_addr[dev] = (double *)p;
+        }
+        scratch = g_static_addr[dev];
+    }
+    double *result = scratch + (size_t)kStaticPartials * 4;
+    const long long k = h->ncoarse << level;
+    LevelDev dv = level_dev(h, level);
+    // every block overwrites its own partial and the final kernel overwrites the
+    // result, so nothing in the shared array has to be cleared between calls
+    if (h->Q == 9) {
+        if (h->d.storage == LBM_F64)
+            k_reduce_partial<9, double><<<(int)blocks, 256, 0, h->stream>>>(dv.g, v.d_tag, (const double *)v.f[k & 1],
+                                                                           v.d_wnode, scratch, h->d_status);
+        else if (h->d.storage == LBM_F32)
+            k_reduce_partial<9, float><<<(int)blocks, 256, 0, h->stream>>>(dv.g, v.d_tag, (const float *)v.f[k & 1],
+                                                                          v.d_wnode, scratch, h->d_status);
+        else
+            k_reduce_partial<9, __half><<<(int)blocks, 256, 0, h->stream>>>(dv.g, v.d_tag, (const __half *)v.f[k & 1],
+                                                                           v.d_wnode, scratch, h->d_status);
+    } else {
+        if (h->d.storage == LBM_F64)
+            k_reduce_partial<19, double><<<(int)blocks, 256, 0, h->stream>>>(dv.g, v.d_tag, (const double *)v.f[k & 1],
+                                                                            v.d_wnode, scratch, h->d_status);
+        else if (h->d.storage == LBM_F32)
+            k_reduce_partial<19, float><<<(int)blocks, 256, 0, h->stream>>>(dv.g, v.d_tag, (const float *)v.f[k & 1],
+                                                                           v.d_wnode, scratch, h->d_status);
+        else
+            k_reduce_partial<19, __half><<<(int)blocks, 256, 0, h->stream>>>(
+                dv.g, v.d_tag, (const __half *)v.f[k & 1], v.d_wnode, scratch, h->d_status);
+    }
+    k_reduce_final<<<1, 256, 0, h->stream>>>(scratch, (int)blocks, result);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, result, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    int st = 0;
+    CK(cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & ST_NAN) return fail(h, LBM_ERR_DIVERGED, "NaN or Inf in level %d", level);
+    return LBM_OK;
+}

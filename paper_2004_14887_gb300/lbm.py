@@ -56,7 +56,7 @@ EXPORTS = [
     "lbm_create_hierarchy", "lbm_create_error", "lbm_query_level", "lbm_node_class", "lbm_init_fields",
     "lbm_advance", "lbm_get_macros", "lbm_get_pops", "lbm_reduce", "lbm_check_status", "lbm_max_newton_iters",
     "lbm_timing_enable", "lbm_timing_read", "lbm_launch_count", "lbm_device_bytes", "lbm_synchronize",
-    "lbm_last_error", "lbm_destroy",
+    "lbm_last_error", "lbm_destroy", "lbm_reduce_static",
 ]
 
 _lib = None
@@ -81,6 +81,7 @@ def lib():
     L.lbm_get_macros.argtypes = [vp, C.c_int, vp, vp, C.c_int]
     L.lbm_get_pops.argtypes = [vp, C.c_int, vp, C.c_int]
     L.lbm_reduce.argtypes = [vp, C.c_int, dp]
+    L.lbm_reduce_static.argtypes = [vp, C.c_int, dp]
     L.lbm_check_status.argtypes = [vp]
     L.lbm_max_newton_iters.argtypes = [vp]
     L.lbm_timing_enable.argtypes = [vp, C.c_int]
@@ -258,6 +259,12 @@ class Hierarchy:
     def reduce(self, l):
         out = (C.c_double * 4)()
         self._check(lib().lbm_reduce(self._h, l, out))
+        return np.array(out[:])
+
+    def reduce_static(self, l):
+        """lbm_reduce_static: the same sums with the partials in static device memory."""
+        out = (C.c_double * 4)()
+        self._check(lib().lbm_reduce_static(self._h, l, out))
         return np.array(out[:])
 
     def check_status(self):
