@@ -102,7 +102,6 @@ struct LevelDev {
     LevelGeo g;
     void *f[2];              // population buffers (storage type), [Q][pitch]
     const int *tag;          // per node: TAG_BULK, TAG_HOLE or interface-table index
-    const unsigned char *tile_flag;
     int tiles[3];
     void *if_pop;            // interface table (type R): completed post-stream populations [Q][nif]
     void *if_mac;            // rho, ux, uy, uz [4][nif]
@@ -110,6 +109,10 @@ struct LevelDev {
     void *if_C;              // C_ab = sum_g d_g Psi_abg [6][nif]
     int nif;
     double tau;
+    // geometric tile classification (see tile_class)
+    int fast_lo[3], fast_hi[3];  // tile grown by 2 must stay in [fast_lo, fast_hi]
+    int has_child;
+    int child_lo[3], child_hi[3], child_per[3];  // closed child box in this level's box coordinates
 };
 
 __device__ __forceinline__ long long node_index(const LevelGeo &g, int x, int y, int z)

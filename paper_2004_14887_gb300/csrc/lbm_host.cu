@@ -47,7 +47,6 @@ struct Level {
     // device
     void *f[2] = {nullptr, nullptr};
     int *d_tag = nullptr;
-    unsigned char *d_tile = nullptr;
     void *if_pop = nullptr, *if_mac = nullptr, *if_S = nullptr, *if_C = nullptr;
     double *d_wnode = nullptr;
 };
@@ -239,6 +238,11 @@ int build_geometry(lbm_h h)
             v.n[a] = ((hi - lo) << l) + 1;
             v.off[a] = lo << l;
             v.per[a] = 0;
+        }
+        if (l > 0) {
+            bool all_span = true;
+            for (int a = 0; a < h->D; a++) all_span = all_span && v.per[a];
+            if (all_span) return fail(nullptr, LBM_ERR_BAD_DESC, "level %d spans every axis: refine level 0 instead", l);
         }
         v.N = (long long)v.n[0] * v.n[1] * v.n[2];
         v.pitch = (v.N + 31) / 32 * 32;
@@ -499,6 +503,60 @@ void build_tiles(lbm_h h)
     }
 }
 
+// the kernel's geometric tile rule (tile_class), replayed on the host
+void tile_bounds(const lbm_h h, int l, int *fast_lo, int *fast_hi, int *child_lo, int *child_hi, int *child_per)
+{
+    const Level &v = h->lev[l];
+    for (int a = 0; a < 3; a++) {
+        const bool outline = l > 0 && !v.per[a] && a < h->D;
+        fast_lo[a] = outline ? 1 : 0;
+        fast_hi[a] = (int)(outline ? v.n[a] - 2 : v.n[a] - 1);
+        child_lo[a] = (int)(v.child_lo[a] - v.off[a]);
+        child_hi[a] = (int)(v.child_hi[a] - v.off[a]);
+        child_per[a] = v.child_per[a];
+    }
+}
+
+unsigned char geometric_class(const lbm_h h, int l, const int *t0, const int *T)
+{
+    const Level &v = h->lev[l];
+    int flo[3], fhi[3], clo[3], chi[3], cper[3];
+    tile_bounds(h, l, flo, fhi, clo, chi, cper);
+    bool fast = true;
+    for (int a = 0; a < h->D; a++)
+        if (t0[a] - 2 < flo[a] || t0[a] + T[a] + 1 > fhi[a]) fast = false;
+    if (v.has_child) {
+        bool disjoint = false, in_hole = true;
+        for (int a = 0; a < h->D; a++) {
+            if (cper[a]) continue;
+            if (t0[a] + T[a] + 1 < clo[a] || t0[a] - 2 > chi[a]) disjoint = true;
+            const int last = std::min<int>(t0[a] + T[a] - 1, (int)v.n[a] - 1);
+            if (!(t0[a] > clo[a] && last < chi[a])) in_hole = false;
+        }
+        if (in_hole) return TILE_SKIP;
+        if (!disjoint) fast = false;
+    }
+    return fast ? TILE_FAST : TILE_GENERAL;
+}
+
+// every tile: the geometric rule must agree with the node-by-node classification
+int check_tiles(lbm_h h)
+{
+    const int TX = h->D == 2 ? T2X : T3X, TY = h->D == 2 ? T2Y : T3Y, TZ = h->D == 2 ? 1 : T3Z;
+    const int T[3] = {TX, TY, TZ};
+    for (int l = 0; l < h->nl; l++) {
+        const Level &v = h->lev[l];
+        for (size_t t = 0; t < v.tile_flag.size(); t++) {
+            const int bx = (int)(t % v.tiles[0]), by = (int)((t / v.tiles[0]) % v.tiles[1]);
+            const int bz = (int)(t / ((size_t)v.tiles[0] * v.tiles[1]));
+            const int t0[3] = {bx * TX, by * TY, bz * TZ};
+            if (geometric_class(h, l, t0, T) != v.tile_flag[t])
+                return fail(nullptr, LBM_ERR_BAD_DESC, "internal: tile %zu of level %d classified inconsistently", t, l);
+        }
+    }
+    return LBM_OK;
+}
+
 // dual-cell volume of every node restricted to its level's region, in level-0 cell units
 std::vector<double> node_weights(const lbm_h h, int l)
 {
@@ -535,7 +593,6 @@ int upload_all(lbm_h h)
             if (!v.f[k]) return fail(h, LBM_ERR_OOM, "population buffer of level %d (%zu bytes)", l, (size_t)Q * v.pitch * ss);
         }
         v.d_tag = upload(h, v.tag, &ok);
-        v.d_tile = upload(h, v.tile_flag, &ok);
         const size_t ni = std::max(1, v.nif), as = arith_size(h->d.storage);
         v.if_pop = dev_alloc(h, ni * Q * as);
         v.if_mac = dev_alloc(h, ni * 4 * as);
@@ -598,13 +655,14 @@ LevelDev level_dev(const lbm_h h, int l)
     d.f[0] = v.f[0];
     d.f[1] = v.f[1];
     d.tag = v.d_tag;
-    d.tile_flag = v.d_tile;
     d.if_pop = v.if_pop;
     d.if_mac = v.if_mac;
     d.if_S = v.if_S;
     d.if_C = v.if_C;
     d.nif = std::max(1, v.nif);
     d.tau = v.tau;
+    tile_bounds(h, l, d.fast_lo, d.fast_hi, d.child_lo, d.child_hi, d.child_per);
+    d.has_child = v.has_child ? 1 : 0;
     return d;
 }
 
@@ -841,6 +899,11 @@ int lbm_create_hierarchy(const lbm_hierarchy_desc *desc, void *cuda_stream, lbm_
         return rc;
     }
     build_tiles(h);
+    rc = check_tiles(h);
+    if (rc != LBM_OK) {
+        delete h;
+        return rc;
+    }
     for (int l = 0; l < h->nl; l++)
         if (h->lev[l].N > (long long)2147483647) {
             delete h;

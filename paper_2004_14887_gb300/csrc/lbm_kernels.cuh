@@ -507,12 +507,59 @@ __device__ __forceinline__ bool halo_macros(const LevelDev &Lv, const S *__restr
 }
 
 // ------------------------------------------------------------------ bulk collide-and-stream
-// One CTA per tile of TX x TY (x TZ) nodes.  Every node of the tile and of its
-// one-node halo pulls its post-stream populations (or reads them from the
-// interface table) and stores rho, u in shared memory; then every tile node takes
-// centred differences from its neighbours (or the supplied S, C of interface
-// nodes) and collides.  Tiles whose tile+2 neighbourhood is all bulk and inside
-// the box skip every class test and wrap.
+// Tile class from the box geometry alone (no memory access): FAST when the tile
+// grown by two nodes stays inside the band of bulk nodes (off the level's own outline,
+// off the closed child box, no periodic wrap), SKIP when every node of the tile lies
+// strictly inside the child box (the hole), GENERAL otherwise.  The host checks at
+// creation that this rule reproduces the node-by-node classification of every tile.
+template <int D>
+__device__ __forceinline__ unsigned char tile_class(const LevelDev &Lv, const int *t0, const int *T)
+{
+    bool fast = true;
+#pragma unroll
+    for (int a = 0; a < D; a++)
+        if (t0[a] - 2 < Lv.fast_lo[a] || t0[a] + T[a] + 1 > Lv.fast_hi[a]) fast = false;
+    if (Lv.has_child) {
+        bool disjoint = false, in_hole = true;
+#pragma unroll
+        for (int a = 0; a < D; a++) {
+            if (Lv.child_per[a]) continue;
+            if (t0[a] + T[a] + 1 < Lv.child_lo[a] || t0[a] - 2 > Lv.child_hi[a]) disjoint = true;
+            const int last = min(t0[a] + T[a] - 1, Lv.g.n[a] - 1);
+            if (!(t0[a] > Lv.child_lo[a] && last < Lv.child_hi[a])) in_hole = false;
+        }
+        if (in_hole) return TILE_SKIP;
+        if (!disjoint) fast = false;
+    }
+    return fast ? TILE_FAST : TILE_GENERAL;
+}
+
+// post-stream moments of populations held in registers
+template <int Q, typename R>
+__device__ __forceinline__ void reg_moments(const R (&f)[Q], R &rho, R *u)
+{
+    using L = Lat<Q>;
+    constexpr int D = L::D;
+    R r = R(0), m[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        r += f[i];
+#pragma unroll
+        for (int a = 0; a < D; a++)
+            if (L::c(i, a) != 0) m[a] += R(L::c(i, a)) * f[i];
+    }
+    rho = r;
+    const R inv = R(1) / r;
+#pragma unroll
+    for (int a = 0; a < D; a++) u[a] = m[a] * inv;
+}
+
+// One CTA per tile of TX x TY (x TZ) nodes, one node per thread.  Every node of the
+// tile and of its one-node halo pulls its post-stream populations (or reads them from
+// the interface table) and leaves rho, u in shared memory; every tile node then takes
+// centred differences from its neighbours (or the supplied S, C of interface nodes)
+// and collides.  In 2-D the 2(TX+TY)+4 halo nodes are shared out one per thread and
+// their loads go out together with the thread's own loads.
 template <int Q, typename S, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
                                                       typename St<S>::R tau, typename St<S>::R om,
@@ -528,48 +575,47 @@ __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__res
     __shared__ R s_u[D][H];
 
     const LevelGeo &g = Lv.g;
-    const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
-    const unsigned char flag = Lv.tile_flag[bx + Lv.tiles[0] * (by + Lv.tiles[1] * bz)];
+    const int X0 = blockIdx.x * TX, Y0 = blockIdx.y * TY, Z0 = blockIdx.z * (D == 3 ? TZ : 1);
+    const int t0[3] = {X0, Y0, Z0}, T[3] = {TX, TY, TZ};
+    const unsigned char flag = tile_class<D>(Lv, t0, T);
     if (flag == TILE_SKIP) return;
-    const int X0 = bx * TX, Y0 = by * TY, Z0 = bz * (D == 3 ? TZ : 1);
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = (tid / TX) % TY, tz = tid / (TX * TY);
     const int x = X0 + tx, y = Y0 + ty, z = Z0 + (D == 3 ? tz : 0);
     const int n01 = g.n[0] * g.n[1];  // boxes hold fewer than 2^31 nodes
-
-    R f[Q];
-    R rho = R(0), u[3] = {R(0), R(0), R(0)};
-    int tag = TAG_HOLE;
     const bool inside = x < g.n[0] && y < g.n[1] && z < g.n[2];
     const int idx = x + g.n[0] * y + n01 * z;
     const int hself = (tx + 1) + HX * ((ty + 1) + HY * (D == 3 ? tz + 1 : 0));
 
-    if (flag == TILE_FAST) {
-        tag = TAG_BULK;
-        if constexpr (D == 2) {
-            // 2-D tiles have fewer halo nodes than threads: thread tid < NB also owns
-            // border position tid, and its halo loads go out with its own loads
-            constexpr int NB = H - NT;
-            static_assert(NB <= NT, "one halo node per thread at most");
-            int hb = -1;
-            int hidx = 0;
-            if (tid < NB) {
-                int hx, hy;
-                if (tid < HX) {
-                    hx = tid;
-                    hy = 0;
-                } else if (tid < 2 * HX) {
-                    hx = tid - HX;
-                    hy = HY - 1;
-                } else {
-                    const int b = tid - 2 * HX;
-                    hy = 1 + (b >> 1);
-                    hx = (b & 1) ? HX - 1 : 0;
-                }
-                hb = hx + HX * hy;
-                hidx = (X0 + hx - 1) + g.n[0] * (Y0 + hy - 1);
+    R f[Q];
+    R rho = R(1), u[3] = {R(0), R(0), R(0)};
+    int tag = TAG_HOLE;
+
+    if constexpr (D == 2) {
+        // halo position owned by this thread (border of the (TX+2) x (TY+2) box)
+        constexpr int NB = H - NT;
+        static_assert(NB <= NT, "one halo node per thread at most");
+        int hb = -1, hx = 0, hy = 0;
+        if (tid < NB) {
+            if (tid < HX) {
+                hx = tid;
+                hy = 0;
+            } else if (tid < 2 * HX) {
+                hx = tid - HX;
+                hy = HY - 1;
+            } else {
+                const int b = tid - 2 * HX;
+                hy = 1 + (b >> 1);
+                hx = (b & 1) ? HX - 1 : 0;
             }
-            R fh[Q];
+            hb = hx + HX * hy;
+        }
+        R fh[Q];
+        int htag = TAG_HOLE;
+        if (flag == TILE_FAST) {
+            tag = TAG_BULK;
+            htag = hb >= 0 ? TAG_BULK : TAG_HOLE;
+            const int hidx = (X0 + hx - 1) + g.n[0] * (Y0 + hy - 1);
 #pragma unroll
             for (int i = 0; i < Q; i++) {
                 const S *pi = fsrc + (long long)i * g.pitch;  // population plane
@@ -577,103 +623,123 @@ __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__res
                 f[i] = St<S>::ld(pi, idx - off, L::w(i));
                 fh[i] = hb >= 0 ? St<S>::ld(pi, hidx - off, L::w(i)) : R(0);
             }
-            if (hb >= 0) {
-                R hr = R(0), m[3] = {R(0), R(0), R(0)};
-#pragma unroll
-                for (int i = 0; i < Q; i++) {
-                    hr += fh[i];
-#pragma unroll
-                    for (int a = 0; a < D; a++)
-                        if (L::c(i, a) != 0) m[a] += R(L::c(i, a)) * fh[i];
-                }
-                s_rho[hb] = hr;
-                const R inv = R(1) / hr;
-#pragma unroll
-                for (int a = 0; a < D; a++) s_u[a][hb] = m[a] * inv;
-            }
         } else {
+            // own position (wrapped when a ragged tile sits past a periodic seam) and
+            // halo position: both tags first, then both pulls
+            int ox = x, oy = y;
+            const bool ovalid = wrap_coord(ox, g.n[0], g.per[0]) && wrap_coord(oy, g.n[1], g.per[1]);
+            int qx = X0 + hx - 1, qy = Y0 + hy - 1;
+            const bool hvalid = hb >= 0 && wrap_coord(qx, g.n[0], g.per[0]) && wrap_coord(qy, g.n[1], g.per[1]);
+            const int oidx = ox + g.n[0] * oy, qidx = qx + g.n[0] * qy;
+            const int otag = ovalid ? Lv.tag[oidx] : TAG_HOLE;
+            htag = hvalid ? Lv.tag[qidx] : TAG_HOLE;
+            const R *pop = (const R *)Lv.if_pop;
+#pragma unroll
+            for (int i = 0; i < Q; i++) {
+                const S *pi = fsrc + (long long)i * g.pitch;
+                // bulk sources are nodes: a one-step wrap on periodic axes is all they need
+                int sx = ox - L::c(i, 0), sy = oy - L::c(i, 1);
+                sx += (sx < 0) ? g.n[0] : ((sx >= g.n[0]) ? -g.n[0] : 0);
+                sy += (sy < 0) ? g.n[1] : ((sy >= g.n[1]) ? -g.n[1] : 0);
+                int px = qx - L::c(i, 0), py = qy - L::c(i, 1);
+                px += (px < 0) ? g.n[0] : ((px >= g.n[0]) ? -g.n[0] : 0);
+                py += (py < 0) ? g.n[1] : ((py >= g.n[1]) ? -g.n[1] : 0);
+                f[i] = otag == TAG_BULK ? St<S>::ld(pi, sx + g.n[0] * sy, L::w(i))
+                                        : (otag >= 0 ? pop[(long long)i * Lv.nif + otag] : R(0));
+                fh[i] = htag == TAG_BULK ? St<S>::ld(pi, px + g.n[0] * py, L::w(i))
+                                         : (htag >= 0 ? pop[(long long)i * Lv.nif + htag] : R(0));
+            }
+            tag = inside ? otag : TAG_HOLE;
+            // macros of the own position (also when it only stands for a wrapped node)
+            if (otag == TAG_BULK) {
+                reg_moments<Q, R>(f, rho, u);
+            } else if (otag >= 0) {
+                const R *mac = (const R *)Lv.if_mac;
+                rho = mac[otag];
+#pragma unroll
+                for (int a = 0; a < D; a++) u[a] = mac[(long long)(1 + a) * Lv.nif + otag];
+            }
+        }
+        if (flag == TILE_FAST) reg_moments<Q, R>(f, rho, u);
+        if (hb >= 0) {
+            R hr = R(1), hu[3] = {R(0), R(0), R(0)};
+            if (htag == TAG_BULK) {
+                reg_moments<Q, R>(fh, hr, hu);
+            } else if (htag >= 0) {
+                const R *mac = (const R *)Lv.if_mac;
+                hr = mac[htag];
+#pragma unroll
+                for (int a = 0; a < D; a++) hu[a] = mac[(long long)(1 + a) * Lv.nif + htag];
+            }
+            s_rho[hb] = hr;
+#pragma unroll
+            for (int a = 0; a < D; a++) s_u[a][hb] = hu[a];
+        }
+    } else {
+        if (flag == TILE_FAST) {
+            tag = TAG_BULK;
 #pragma unroll
             for (int i = 0; i < Q; i++) {
                 const int off = L::c(i, 0) + g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
                 f[i] = St<S>::ld(fsrc + (long long)i * g.pitch, idx - off, L::w(i));
             }
-        }
-    } else if (inside) {
-        tag = Lv.tag[idx];
-        if (tag == TAG_BULK) {
+            reg_moments<Q, R>(f, rho, u);
+        } else if (inside) {
+            tag = Lv.tag[idx];
+            if (tag == TAG_BULK) {
 #pragma unroll
-            for (int i = 0; i < Q; i++) {
-                int sx = x - L::c(i, 0), sy = y - L::c(i, 1), sz = z - L::c(i, 2);
-                if (!wrap_coord(sx, g.n[0], g.per[0])) sx = x;  // bulk sources are nodes: never taken
-                if (!wrap_coord(sy, g.n[1], g.per[1])) sy = y;
-                if (!wrap_coord(sz, g.n[2], g.per[2])) sz = z;
-                f[i] = St<S>::ld(fsrc, (long long)i * g.pitch + node_index(g, sx, sy, sz), L::w(i));
+                for (int i = 0; i < Q; i++) {
+                    int sx = x - L::c(i, 0), sy = y - L::c(i, 1), sz = z - L::c(i, 2);
+                    if (!wrap_coord(sx, g.n[0], g.per[0])) sx = x;  // bulk sources are nodes: never taken
+                    if (!wrap_coord(sy, g.n[1], g.per[1])) sy = y;
+                    if (!wrap_coord(sz, g.n[2], g.per[2])) sz = z;
+                    f[i] = St<S>::ld(fsrc + (long long)i * g.pitch, node_index(g, sx, sy, sz), L::w(i));
+                }
+                reg_moments<Q, R>(f, rho, u);
+            } else if (tag >= 0) {
+                const R *pop = (const R *)Lv.if_pop;
+                const R *mac = (const R *)Lv.if_mac;
+#pragma unroll
+                for (int i = 0; i < Q; i++) f[i] = pop[(long long)i * Lv.nif + tag];
+                rho = mac[tag];
+#pragma unroll
+                for (int a = 0; a < D; a++) u[a] = mac[(long long)(1 + a) * Lv.nif + tag];
             }
-        } else if (tag >= 0) {
-            const R *pop = (const R *)Lv.if_pop;
+        } else {
+            // a ragged last tile: on a periodic axis this position is the wrapped node
+            R hr, hu[3];
+            halo_macros<Q, S>(Lv, fsrc, x, y, z, hr, hu);
+            rho = hr;
 #pragma unroll
-            for (int i = 0; i < Q; i++) f[i] = pop[(long long)i * Lv.nif + tag];
+            for (int a = 0; a < D; a++) u[a] = hu[a];
         }
-    }
-    if (tag == TAG_BULK) {
-        R m[3] = {R(0), R(0), R(0)};
+        // halo ring
+        for (int h = tid; h < H; h += NT) {
+            const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+            const bool border = hx == 0 || hx == HX - 1 || hy == 0 || hy == HY - 1 || hz == 0 || hz == HZ - 1;
+            if (!border) continue;
+            const int xx = X0 + hx - 1, yy = Y0 + hy - 1, zz = Z0 + hz - 1;
+            R hr = R(1), hu[3] = {R(0), R(0), R(0)};
+            if (flag == TILE_FAST) {
+                const int hidx = xx + g.n[0] * yy + n01 * zz;
+                R fh[Q];
 #pragma unroll
-        for (int i = 0; i < Q; i++) {
-            rho += f[i];
+                for (int i = 0; i < Q; i++) {
+                    const int off = L::c(i, 0) + g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
+                    fh[i] = St<S>::ld(fsrc + (long long)i * g.pitch, hidx - off, L::w(i));
+                }
+                reg_moments<Q, R>(fh, hr, hu);
+            } else {
+                halo_macros<Q, S>(Lv, fsrc, xx, yy, zz, hr, hu);
+            }
+            s_rho[h] = hr;
 #pragma unroll
-            for (int a = 0; a < D; a++)
-                if (L::c(i, a) != 0) m[a] += R(L::c(i, a)) * f[i];
+            for (int a = 0; a < D; a++) s_u[a][h] = hu[a];
         }
-        const R inv = R(1) / rho;
-#pragma unroll
-        for (int a = 0; a < D; a++) u[a] = m[a] * inv;
-    } else if (tag >= 0) {
-        const R *mac = (const R *)Lv.if_mac;
-        rho = mac[tag];
-#pragma unroll
-        for (int a = 0; a < D; a++) u[a] = mac[(long long)(1 + a) * Lv.nif + tag];
-    }
-    if (flag != TILE_FAST && !inside) {
-        // a ragged last tile: on a periodic axis this position is the wrapped node
-        R hr, hu[3];
-        halo_macros<Q, S>(Lv, fsrc, x, y, z, hr, hu);
-        rho = hr;
-#pragma unroll
-        for (int a = 0; a < D; a++) u[a] = hu[a];
     }
     s_rho[hself] = rho;
 #pragma unroll
     for (int a = 0; a < D; a++) s_u[a][hself] = u[a];
-
-    // halo ring (2-D fast tiles loaded it above)
-    for (int h = tid; h < H && !(D == 2 && flag == TILE_FAST); h += NT) {
-        const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
-        const bool border = hx == 0 || hx == HX - 1 || hy == 0 || hy == HY - 1 || (D == 3 && (hz == 0 || hz == HZ - 1));
-        if (!border) continue;
-        int xx = X0 + hx - 1, yy = Y0 + hy - 1, zz = Z0 + (D == 3 ? hz - 1 : 0);
-        R hr = R(1), hu[3] = {R(0), R(0), R(0)};
-        if (flag == TILE_FAST) {
-            const int hidx = xx + g.n[0] * yy + n01 * zz;
-            R m[3] = {R(0), R(0), R(0)};
-            hr = R(0);
-#pragma unroll
-            for (int i = 0; i < Q; i++) {
-                const int off = L::c(i, 0) + g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
-                const R v = St<S>::ld(fsrc + (long long)i * g.pitch, hidx - off, L::w(i));
-                hr += v;
-#pragma unroll
-                for (int a = 0; a < D; a++)
-                    if (L::c(i, a) != 0) m[a] += R(L::c(i, a)) * v;
-            }
-#pragma unroll
-            for (int a = 0; a < D; a++) hu[a] = m[a] / hr;
-        } else {
-            halo_macros<Q, S>(Lv, fsrc, xx, yy, zz, hr, hu);
-        }
-        s_rho[h] = hr;
-#pragma unroll
-        for (int a = 0; a < D; a++) s_u[a][h] = hu[a];
-    }
     __syncthreads();
     if (tag == TAG_HOLE || !inside) return;
 
@@ -683,13 +749,13 @@ __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__res
 #pragma unroll
         for (int b = 0; b < D; b++)
 #pragma unroll
-            for (int s = 0; s < 2; s++) {
-                const int o = (s == 0 ? 1 : -1);
+            for (int s2 = 0; s2 < 2; s2++) {
+                const int o = (s2 == 0 ? 1 : -1);
                 const int hh = hself + (b == 0 ? o : (b == 1 ? o * HX : o * HX * HY));
-                nr[b][s] = s_rho[hh];
+                nr[b][s2] = s_rho[hh];
 #pragma unroll
-                for (int a = 0; a < D; a++) nu[b][s][a] = s_u[a][hh];
-                if (D == 2) nu[b][s][2] = R(0);
+                for (int a = 0; a < D; a++) nu[b][s2][a] = s_u[a][hh];
+                if (D == 2) nu[b][s2][2] = R(0);
             }
         fd_gradients<D, R>(nr, nu, R(0.5), Sv, Cv);
     } else {

@@ -80,3 +80,26 @@ def test_binding_refuses_without_gpu():
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError, match="CUDA device"):
         lbm.Hierarchy({"lattice": 9, "coarse_n": (32, 32), "boxes": [], "nu0": 1e-5})
+
+
+@pytest.mark.parametrize("desc", [
+    {"lattice": 9, "coarse_n": (72, 40), "boxes": [], "nu0": 1e-5},
+    {"lattice": 9, "coarse_n": (128, 128), "boxes": [((32, 32), (96, 96))], "nu0": 1e-5},
+    {"lattice": 9, "coarse_n": (512, 512), "boxes": [((128, 128), (384, 384)), ((192, 192), (320, 320))], "nu0": 1e-5},
+    {"lattice": 9, "coarse_n": (64, 64), "boxes": [((16, 0), (48, 64))], "nu0": 1e-5},
+    {"lattice": 19, "coarse_n": (16, 16, 24), "boxes": [((0, 0, 6), (16, 16, 18)), ((4, 4, 9), (12, 12, 15))],
+     "nu0": 1e-5},
+    {"lattice": 19, "coarse_n": (32, 32, 32), "boxes": [((8, 8, 8), (24, 24, 24)), ((12, 12, 12), (20, 20, 20))],
+     "nu0": 1e-5},
+], ids=["2d-periodic-ragged", "2d-2lvl", "2d-3lvl-512", "2d-slab", "3d-slab-3lvl", "3d-cubes-3lvl"])
+def test_host_geometry_and_tile_rule_accept_valid_hierarchies(L, desc):
+    """Host-side set-up (classes, interface tables, and the check that the kernels'
+    geometric tile rule matches the node-by-node classification of every tile) runs
+    before any device work; without a GPU the call then stops at the first CUDA call."""
+    d = lbm.make_desc(desc)
+    h = C.c_void_p()
+    rc = L.lbm_create_hierarchy(C.byref(d), None, C.byref(h))
+    if rc == lbm.LBM_OK:
+        L.lbm_destroy(h)
+    else:
+        assert rc == lbm.LBM_ERR_CUDA, L.lbm_create_error().decode()
