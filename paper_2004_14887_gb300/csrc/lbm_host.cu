@@ -466,7 +466,8 @@ int build_interfaces(lbm_h h)
     return LBM_OK;
 }
 
-constexpr int T2X = 32, T2Y = 8;             // D2Q9 tile
+constexpr int T2X = 32, T2YT = 8, T2NR = 2;  // D2Q9 tile: 32 x 8 threads, 2 rows per thread
+constexpr int T2Y = T2YT * T2NR;
 constexpr int T3X = 32, T3Y = 4, T3Z = 2;    // D3Q19 tile
 
 void build_tiles(lbm_h h)
@@ -687,8 +688,8 @@ struct Sched {
         using R = typename St<S>::R;
         const R tau = (R)v.tau, om = (R)(1.0 - 1.0 / v.tau), sig = (R)h->d.sigma, sps = (R)spsi;
         if constexpr (Lat<Q>::D == 2)
-            k_bulk<Q, S, T2X, T2Y, 1><<<nt, T2X * T2Y, 0, h->stream>>>(level_dev(h, l), (const S *)src, (S *)dst, tau,
-                                                                      om, sig, sps);
+            k_bulk2d<Q, S, T2X, T2YT, T2NR><<<nt, T2X * T2YT, 0, h->stream>>>(level_dev(h, l), (const S *)src,
+                                                                             (S *)dst, tau, om, sig, sps);
         else
             k_bulk<Q, S, T3X, T3Y, T3Z><<<nt, T3X * T3Y * T3Z, 0, h->stream>>>(level_dev(h, l), (const S *)src,
                                                                               (S *)dst, tau, om, sig, sps);

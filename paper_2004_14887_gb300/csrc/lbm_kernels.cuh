@@ -554,195 +554,18 @@ __device__ __forceinline__ void reg_moments(const R (&f)[Q], R &rho, R *u)
     for (int a = 0; a < D; a++) u[a] = m[a] * inv;
 }
 
-// One CTA per tile of TX x TY (x TZ) nodes, one node per thread.  Every node of the
-// tile and of its one-node halo pulls its post-stream populations (or reads them from
-// the interface table) and leaves rho, u in shared memory; every tile node then takes
-// centred differences from its neighbours (or the supplied S, C of interface nodes)
-// and collides.  In 2-D the 2(TX+TY)+4 halo nodes are shared out one per thread and
-// their loads go out together with the thread's own loads.
-template <int Q, typename S, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
-                                                      typename St<S>::R tau, typename St<S>::R om,
-                                                      typename St<S>::R sigma, typename St<S>::R spsi)
+// Collision of one node from the shared-memory macros (bulk) or the interface table,
+// then the store.
+template <int Q, typename S, int HX, int HY, int HPLANE>
+__device__ __forceinline__ void collide_store(const LevelDev &Lv, typename St<S>::R (&f)[Q], typename St<S>::R rho,
+                                              const typename St<S>::R *u, int tag, int hself,
+                                              const typename St<S>::R *s_rho, const typename St<S>::R *s_u,
+                                              typename St<S>::R tau, typename St<S>::R om, typename St<S>::R sigma,
+                                              typename St<S>::R spsi, S *__restrict__ fdst, int idx)
 {
     using L = Lat<Q>;
     using R = typename St<S>::R;
     constexpr int D = L::D;
-    constexpr int HX = TX + 2, HY = TY + 2, HZ = (D == 3) ? TZ + 2 : 1;
-    constexpr int H = HX * HY * HZ;
-    constexpr int NT = TX * TY * TZ;
-    __shared__ R s_rho[H];
-    __shared__ R s_u[D][H];
-
-    const LevelGeo &g = Lv.g;
-    const int X0 = blockIdx.x * TX, Y0 = blockIdx.y * TY, Z0 = blockIdx.z * (D == 3 ? TZ : 1);
-    const int t0[3] = {X0, Y0, Z0}, T[3] = {TX, TY, TZ};
-    const unsigned char flag = tile_class<D>(Lv, t0, T);
-    if (flag == TILE_SKIP) return;
-    const int tid = threadIdx.x;
-    const int tx = tid % TX, ty = (tid / TX) % TY, tz = tid / (TX * TY);
-    const int x = X0 + tx, y = Y0 + ty, z = Z0 + (D == 3 ? tz : 0);
-    const int n01 = g.n[0] * g.n[1];  // boxes hold fewer than 2^31 nodes
-    const bool inside = x < g.n[0] && y < g.n[1] && z < g.n[2];
-    const int idx = x + g.n[0] * y + n01 * z;
-    const int hself = (tx + 1) + HX * ((ty + 1) + HY * (D == 3 ? tz + 1 : 0));
-
-    R f[Q];
-    R rho = R(1), u[3] = {R(0), R(0), R(0)};
-    int tag = TAG_HOLE;
-
-    if constexpr (D == 2) {
-        // halo position owned by this thread (border of the (TX+2) x (TY+2) box)
-        constexpr int NB = H - NT;
-        static_assert(NB <= NT, "one halo node per thread at most");
-        int hb = -1, hx = 0, hy = 0;
-        if (tid < NB) {
-            if (tid < HX) {
-                hx = tid;
-                hy = 0;
-            } else if (tid < 2 * HX) {
-                hx = tid - HX;
-                hy = HY - 1;
-            } else {
-                const int b = tid - 2 * HX;
-                hy = 1 + (b >> 1);
-                hx = (b & 1) ? HX - 1 : 0;
-            }
-            hb = hx + HX * hy;
-        }
-        R fh[Q];
-        int htag = TAG_HOLE;
-        if (flag == TILE_FAST) {
-            tag = TAG_BULK;
-            htag = hb >= 0 ? TAG_BULK : TAG_HOLE;
-            const int hidx = (X0 + hx - 1) + g.n[0] * (Y0 + hy - 1);
-#pragma unroll
-            for (int i = 0; i < Q; i++) {
-                const S *pi = fsrc + (long long)i * g.pitch;  // population plane
-                const int off = L::c(i, 0) + g.n[0] * L::c(i, 1);
-                f[i] = St<S>::ld(pi, idx - off, L::w(i));
-                fh[i] = hb >= 0 ? St<S>::ld(pi, hidx - off, L::w(i)) : R(0);
-            }
-        } else {
-            // own position (wrapped when a ragged tile sits past a periodic seam) and
-            // halo position: both tags first, then both pulls
-            int ox = x, oy = y;
-            const bool ovalid = wrap_coord(ox, g.n[0], g.per[0]) && wrap_coord(oy, g.n[1], g.per[1]);
-            int qx = X0 + hx - 1, qy = Y0 + hy - 1;
-            const bool hvalid = hb >= 0 && wrap_coord(qx, g.n[0], g.per[0]) && wrap_coord(qy, g.n[1], g.per[1]);
-            const int oidx = ox + g.n[0] * oy, qidx = qx + g.n[0] * qy;
-            const int otag = ovalid ? Lv.tag[oidx] : TAG_HOLE;
-            htag = hvalid ? Lv.tag[qidx] : TAG_HOLE;
-            const R *pop = (const R *)Lv.if_pop;
-#pragma unroll
-            for (int i = 0; i < Q; i++) {
-                const S *pi = fsrc + (long long)i * g.pitch;
-                // bulk sources are nodes: a one-step wrap on periodic axes is all they need
-                int sx = ox - L::c(i, 0), sy = oy - L::c(i, 1);
-                sx += (sx < 0) ? g.n[0] : ((sx >= g.n[0]) ? -g.n[0] : 0);
-                sy += (sy < 0) ? g.n[1] : ((sy >= g.n[1]) ? -g.n[1] : 0);
-                int px = qx - L::c(i, 0), py = qy - L::c(i, 1);
-                px += (px < 0) ? g.n[0] : ((px >= g.n[0]) ? -g.n[0] : 0);
-                py += (py < 0) ? g.n[1] : ((py >= g.n[1]) ? -g.n[1] : 0);
-                f[i] = otag == TAG_BULK ? St<S>::ld(pi, sx + g.n[0] * sy, L::w(i))
-                                        : (otag >= 0 ? pop[(long long)i * Lv.nif + otag] : R(0));
-                fh[i] = htag == TAG_BULK ? St<S>::ld(pi, px + g.n[0] * py, L::w(i))
-                                         : (htag >= 0 ? pop[(long long)i * Lv.nif + htag] : R(0));
-            }
-            tag = inside ? otag : TAG_HOLE;
-            // macros of the own position (also when it only stands for a wrapped node)
-            if (otag == TAG_BULK) {
-                reg_moments<Q, R>(f, rho, u);
-            } else if (otag >= 0) {
-                const R *mac = (const R *)Lv.if_mac;
-                rho = mac[otag];
-#pragma unroll
-                for (int a = 0; a < D; a++) u[a] = mac[(long long)(1 + a) * Lv.nif + otag];
-            }
-        }
-        if (flag == TILE_FAST) reg_moments<Q, R>(f, rho, u);
-        if (hb >= 0) {
-            R hr = R(1), hu[3] = {R(0), R(0), R(0)};
-            if (htag == TAG_BULK) {
-                reg_moments<Q, R>(fh, hr, hu);
-            } else if (htag >= 0) {
-                const R *mac = (const R *)Lv.if_mac;
-                hr = mac[htag];
-#pragma unroll
-                for (int a = 0; a < D; a++) hu[a] = mac[(long long)(1 + a) * Lv.nif + htag];
-            }
-            s_rho[hb] = hr;
-#pragma unroll
-            for (int a = 0; a < D; a++) s_u[a][hb] = hu[a];
-        }
-    } else {
-        if (flag == TILE_FAST) {
-            tag = TAG_BULK;
-#pragma unroll
-            for (int i = 0; i < Q; i++) {
-                const int off = L::c(i, 0) + g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
-                f[i] = St<S>::ld(fsrc + (long long)i * g.pitch, idx - off, L::w(i));
-            }
-            reg_moments<Q, R>(f, rho, u);
-        } else if (inside) {
-            tag = Lv.tag[idx];
-            if (tag == TAG_BULK) {
-#pragma unroll
-                for (int i = 0; i < Q; i++) {
-                    int sx = x - L::c(i, 0), sy = y - L::c(i, 1), sz = z - L::c(i, 2);
-                    if (!wrap_coord(sx, g.n[0], g.per[0])) sx = x;  // bulk sources are nodes: never taken
-                    if (!wrap_coord(sy, g.n[1], g.per[1])) sy = y;
-                    if (!wrap_coord(sz, g.n[2], g.per[2])) sz = z;
-                    f[i] = St<S>::ld(fsrc + (long long)i * g.pitch, node_index(g, sx, sy, sz), L::w(i));
-                }
-                reg_moments<Q, R>(f, rho, u);
-            } else if (tag >= 0) {
-                const R *pop = (const R *)Lv.if_pop;
-                const R *mac = (const R *)Lv.if_mac;
-#pragma unroll
-                for (int i = 0; i < Q; i++) f[i] = pop[(long long)i * Lv.nif + tag];
-                rho = mac[tag];
-#pragma unroll
-                for (int a = 0; a < D; a++) u[a] = mac[(long long)(1 + a) * Lv.nif + tag];
-            }
-        } else {
-            // a ragged last tile: on a periodic axis this position is the wrapped node
-            R hr, hu[3];
-            halo_macros<Q, S>(Lv, fsrc, x, y, z, hr, hu);
-            rho = hr;
-#pragma unroll
-            for (int a = 0; a < D; a++) u[a] = hu[a];
-        }
-        // halo ring
-        for (int h = tid; h < H; h += NT) {
-            const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
-            const bool border = hx == 0 || hx == HX - 1 || hy == 0 || hy == HY - 1 || hz == 0 || hz == HZ - 1;
-            if (!border) continue;
-            const int xx = X0 + hx - 1, yy = Y0 + hy - 1, zz = Z0 + hz - 1;
-            R hr = R(1), hu[3] = {R(0), R(0), R(0)};
-            if (flag == TILE_FAST) {
-                const int hidx = xx + g.n[0] * yy + n01 * zz;
-                R fh[Q];
-#pragma unroll
-                for (int i = 0; i < Q; i++) {
-                    const int off = L::c(i, 0) + g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
-                    fh[i] = St<S>::ld(fsrc + (long long)i * g.pitch, hidx - off, L::w(i));
-                }
-                reg_moments<Q, R>(fh, hr, hu);
-            } else {
-                halo_macros<Q, S>(Lv, fsrc, xx, yy, zz, hr, hu);
-            }
-            s_rho[h] = hr;
-#pragma unroll
-            for (int a = 0; a < D; a++) s_u[a][h] = hu[a];
-        }
-    }
-    s_rho[hself] = rho;
-#pragma unroll
-    for (int a = 0; a < D; a++) s_u[a][hself] = u[a];
-    __syncthreads();
-    if (tag == TAG_HOLE || !inside) return;
-
     R Sv[6], Cv[6];
     if (tag == TAG_BULK) {
         R nr[3][2], nu[3][2][3];
@@ -754,7 +577,7 @@ __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__res
                 const int hh = hself + (b == 0 ? o : (b == 1 ? o * HX : o * HX * HY));
                 nr[b][s2] = s_rho[hh];
 #pragma unroll
-                for (int a = 0; a < D; a++) nu[b][s2][a] = s_u[a][hh];
+                for (int a = 0; a < D; a++) nu[b][s2][a] = s_u[a * HPLANE + hh];
                 if (D == 2) nu[b][s2][2] = R(0);
             }
         fd_gradients<D, R>(nr, nu, R(0.5), Sv, Cv);
@@ -768,7 +591,267 @@ __global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__res
     }
     hrr_collide<Q, R>(f, rho, u, Sv, Cv, tau, om, sigma, spsi);
 #pragma unroll
-    for (int i = 0; i < Q; i++) St<S>::st(fdst + (long long)i * g.pitch, idx, f[i], L::w(i));
+    for (int i = 0; i < Q; i++) St<S>::st(fdst + (long long)i * Lv.g.pitch, idx, f[i], L::w(i));
+}
+
+// 2-D: one CTA per tile of TX x (TYT*NR) nodes, TX x TYT threads, NR nodes per thread
+// (rows ty, ty+TYT, ...).  Every node of the tile and of its one-node halo pulls its
+// post-stream populations (or reads them from the interface table) and leaves rho, u
+// in shared memory; every tile node then takes centred differences from its
+// neighbours (or the supplied S, C of interface nodes) and collides.  The
+// 2(TX+TY)+4 halo nodes are shared out one per thread; all loads of a thread (its
+// nodes and its halo node) go out before any is used.
+template <int Q, typename S, int TX, int TYT, int NR>
+__global__ void __launch_bounds__(TX *TYT) k_bulk2d(LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
+                                                     typename St<S>::R tau, typename St<S>::R om,
+                                                     typename St<S>::R sigma, typename St<S>::R spsi)
+{
+    using L = Lat<Q>;
+    using R = typename St<S>::R;
+    constexpr int D = 2;
+    static_assert(L::D == 2, "2-D kernel");
+    constexpr int TY = TYT * NR;
+    constexpr int HX = TX + 2, HY = TY + 2;
+    constexpr int H = HX * HY;
+    constexpr int NT = TX * TYT;
+    constexpr int NB = 2 * HX + 2 * TY;  // halo positions
+    static_assert(NB <= NT, "one halo node per thread at most");
+    __shared__ R s_rho[H];
+    __shared__ R s_u[D * H];
+
+    const LevelGeo &g = Lv.g;
+    const int X0 = blockIdx.x * TX, Y0 = blockIdx.y * TY;
+    const int t0[3] = {X0, Y0, 0}, T[3] = {TX, TY, 1};
+    const unsigned char flag = tile_class<D>(Lv, t0, T);
+    if (flag == TILE_SKIP) return;
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, tr = tid / TX;
+    const int x = X0 + tx;
+
+    // halo position owned by this thread
+    int hb = -1, hx = 0, hy = 0;
+    if (tid < NB) {
+        if (tid < HX) {
+            hx = tid;
+            hy = 0;
+        } else if (tid < 2 * HX) {
+            hx = tid - HX;
+            hy = HY - 1;
+        } else {
+            const int b = tid - 2 * HX;
+            hy = 1 + (b >> 1);
+            hx = (b & 1) ? HX - 1 : 0;
+        }
+        hb = hx + HX * hy;
+    }
+
+    R f[NR][Q], fh[Q];
+    int tag[NR];
+    int htag = TAG_HOLE;
+    bool inside[NR];
+    int idx[NR];
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+        const int y = Y0 + tr + r * TYT;
+        inside[r] = x < g.n[0] && y < g.n[1];
+        idx[r] = x + g.n[0] * y;
+    }
+    int otag[NR];
+    if (flag == TILE_FAST) {
+#pragma unroll
+        for (int r = 0; r < NR; r++) otag[r] = TAG_BULK;
+        htag = hb >= 0 ? TAG_BULK : TAG_HOLE;
+        const int hidx = (X0 + hx - 1) + g.n[0] * (Y0 + hy - 1);
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const S *pi = fsrc + (long long)i * g.pitch;  // population plane
+            const int off = L::c(i, 0) + g.n[0] * L::c(i, 1);
+#pragma unroll
+            for (int r = 0; r < NR; r++) f[r][i] = St<S>::ld(pi, idx[r] - off, L::w(i));
+        }
+        if (hb >= 0) {
+#pragma unroll
+            for (int i = 0; i < Q; i++) {
+                const int off = L::c(i, 0) + g.n[0] * L::c(i, 1);
+                fh[i] = St<S>::ld(fsrc + (long long)i * g.pitch, hidx - off, L::w(i));
+            }
+        }
+    } else {
+        // own positions (wrapped when a ragged tile sits past a periodic seam) and the
+        // halo position: tags first, then every pull
+        int ox[NR], oy[NR];
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+            ox[r] = x;
+            oy[r] = Y0 + tr + r * TYT;
+            const bool ok = wrap_coord(ox[r], g.n[0], g.per[0]) && wrap_coord(oy[r], g.n[1], g.per[1]);
+            otag[r] = ok ? Lv.tag[ox[r] + g.n[0] * oy[r]] : TAG_HOLE;
+        }
+        int qx = X0 + hx - 1, qy = Y0 + hy - 1;
+        const bool hvalid = hb >= 0 && wrap_coord(qx, g.n[0], g.per[0]) && wrap_coord(qy, g.n[1], g.per[1]);
+        htag = hvalid ? Lv.tag[qx + g.n[0] * qy] : TAG_HOLE;
+        const R *pop = (const R *)Lv.if_pop;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const S *pi = fsrc + (long long)i * g.pitch;
+#pragma unroll
+            for (int r = 0; r < NR; r++) {
+                // bulk sources are nodes: a one-step wrap on periodic axes is all they need
+                int sx = ox[r] - L::c(i, 0), sy = oy[r] - L::c(i, 1);
+                sx += (sx < 0) ? g.n[0] : ((sx >= g.n[0]) ? -g.n[0] : 0);
+                sy += (sy < 0) ? g.n[1] : ((sy >= g.n[1]) ? -g.n[1] : 0);
+                f[r][i] = otag[r] == TAG_BULK ? St<S>::ld(pi, sx + g.n[0] * sy, L::w(i))
+                                              : (otag[r] >= 0 ? pop[(long long)i * Lv.nif + otag[r]] : R(0));
+            }
+            int px = qx - L::c(i, 0), py = qy - L::c(i, 1);
+            px += (px < 0) ? g.n[0] : ((px >= g.n[0]) ? -g.n[0] : 0);
+            py += (py < 0) ? g.n[1] : ((py >= g.n[1]) ? -g.n[1] : 0);
+            fh[i] = htag == TAG_BULK ? St<S>::ld(pi, px + g.n[0] * py, L::w(i))
+                                     : (htag >= 0 ? pop[(long long)i * Lv.nif + htag] : R(0));
+        }
+    }
+    // macros of every own position (a position past a periodic seam stands for the
+    // wrapped node) and of the halo position
+    R rho[NR], u[NR][3];
+    const R *mac = (const R *)Lv.if_mac;
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+        rho[r] = R(1);
+        u[r][0] = u[r][1] = u[r][2] = R(0);
+        if (otag[r] == TAG_BULK) {
+            reg_moments<Q, R>(f[r], rho[r], u[r]);
+        } else if (otag[r] >= 0) {
+            rho[r] = mac[otag[r]];
+#pragma unroll
+            for (int a = 0; a < D; a++) u[r][a] = mac[(long long)(1 + a) * Lv.nif + otag[r]];
+        }
+        tag[r] = inside[r] ? otag[r] : TAG_HOLE;
+        const int hs = (tx + 1) + HX * (tr + r * TYT + 1);
+        s_rho[hs] = rho[r];
+#pragma unroll
+        for (int a = 0; a < D; a++) s_u[a * H + hs] = u[r][a];
+    }
+    if (hb >= 0) {
+        R hr = R(1), hu[3] = {R(0), R(0), R(0)};
+        if (htag == TAG_BULK) {
+            reg_moments<Q, R>(fh, hr, hu);
+        } else if (htag >= 0) {
+            hr = mac[htag];
+#pragma unroll
+            for (int a = 0; a < D; a++) hu[a] = mac[(long long)(1 + a) * Lv.nif + htag];
+        }
+        s_rho[hb] = hr;
+#pragma unroll
+        for (int a = 0; a < D; a++) s_u[a * H + hb] = hu[a];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+        if (tag[r] == TAG_HOLE) continue;
+        const int hs = (tx + 1) + HX * (tr + r * TYT + 1);
+        collide_store<Q, S, HX, HY, H>(Lv, f[r], rho[r], u[r], tag[r], hs, s_rho, s_u, tau, om, sigma, spsi, fdst,
+                                       idx[r]);
+    }
+}
+
+// 3-D: one CTA per tile of TX x TY x TZ nodes, one node per thread.
+template <int Q, typename S, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
+                                                      typename St<S>::R tau, typename St<S>::R om,
+                                                      typename St<S>::R sigma, typename St<S>::R spsi)
+{
+    using L = Lat<Q>;
+    using R = typename St<S>::R;
+    constexpr int D = L::D;
+    static_assert(D == 3, "3-D kernel");
+    constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
+    constexpr int H = HX * HY * HZ;
+    constexpr int NT = TX * TY * TZ;
+    __shared__ R s_rho[H];
+    __shared__ R s_u[D][H];
+
+    const LevelGeo &g = Lv.g;
+    const int X0 = blockIdx.x * TX, Y0 = blockIdx.y * TY, Z0 = blockIdx.z * TZ;
+    const int t0[3] = {X0, Y0, Z0}, T[3] = {TX, TY, TZ};
+    const unsigned char flag = tile_class<D>(Lv, t0, T);
+    if (flag == TILE_SKIP) return;
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = (tid / TX) % TY, tz = tid / (TX * TY);
+    const int x = X0 + tx, y = Y0 + ty, z = Z0 + tz;
+    const int n01 = g.n[0] * g.n[1];  // boxes hold fewer than 2^31 nodes
+    const bool inside = x < g.n[0] && y < g.n[1] && z < g.n[2];
+    const int idx = x + g.n[0] * y + n01 * z;
+    const int hself = (tx + 1) + HX * ((ty + 1) + HY * (tz + 1));
+
+    R f[Q];
+    R rho = R(1), u[3] = {R(0), R(0), R(0)};
+    int tag = TAG_HOLE;
+    if (flag == TILE_FAST) {
+        tag = TAG_BULK;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const int off = L::c(i, 0) + g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
+            f[i] = St<S>::ld(fsrc + (long long)i * g.pitch, idx - off, L::w(i));
+        }
+        reg_moments<Q, R>(f, rho, u);
+    } else if (inside) {
+        tag = Lv.tag[idx];
+        if (tag == TAG_BULK) {
+#pragma unroll
+            for (int i = 0; i < Q; i++) {
+                int sx = x - L::c(i, 0), sy = y - L::c(i, 1), sz = z - L::c(i, 2);
+                if (!wrap_coord(sx, g.n[0], g.per[0])) sx = x;  // bulk sources are nodes: never taken
+                if (!wrap_coord(sy, g.n[1], g.per[1])) sy = y;
+                if (!wrap_coord(sz, g.n[2], g.per[2])) sz = z;
+                f[i] = St<S>::ld(fsrc + (long long)i * g.pitch, node_index(g, sx, sy, sz), L::w(i));
+            }
+            reg_moments<Q, R>(f, rho, u);
+        } else if (tag >= 0) {
+            const R *pop = (const R *)Lv.if_pop;
+            const R *mac = (const R *)Lv.if_mac;
+#pragma unroll
+            for (int i = 0; i < Q; i++) f[i] = pop[(long long)i * Lv.nif + tag];
+            rho = mac[tag];
+#pragma unroll
+            for (int a = 0; a < D; a++) u[a] = mac[(long long)(1 + a) * Lv.nif + tag];
+        }
+    } else {
+        // a ragged last tile: on a periodic axis this position is the wrapped node
+        R hr, hu[3];
+        halo_macros<Q, S>(Lv, fsrc, x, y, z, hr, hu);
+        rho = hr;
+#pragma unroll
+        for (int a = 0; a < D; a++) u[a] = hu[a];
+    }
+    // halo ring
+    for (int h = tid; h < H; h += NT) {
+        const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+        const bool border = hx == 0 || hx == HX - 1 || hy == 0 || hy == HY - 1 || hz == 0 || hz == HZ - 1;
+        if (!border) continue;
+        const int xx = X0 + hx - 1, yy = Y0 + hy - 1, zz = Z0 + hz - 1;
+        R hr = R(1), hu[3] = {R(0), R(0), R(0)};
+        if (flag == TILE_FAST) {
+            const int hidx = xx + g.n[0] * yy + n01 * zz;
+            R fh[Q];
+#pragma unroll
+            for (int i = 0; i < Q; i++) {
+                const int off = L::c(i, 0) + g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
+                fh[i] = St<S>::ld(fsrc + (long long)i * g.pitch, hidx - off, L::w(i));
+            }
+            reg_moments<Q, R>(fh, hr, hu);
+        } else {
+            halo_macros<Q, S>(Lv, fsrc, xx, yy, zz, hr, hu);
+        }
+        s_rho[h] = hr;
+#pragma unroll
+        for (int a = 0; a < D; a++) s_u[a][h] = hu[a];
+    }
+    s_rho[hself] = rho;
+#pragma unroll
+    for (int a = 0; a < D; a++) s_u[a][hself] = u[a];
+    __syncthreads();
+    if (tag == TAG_HOLE || !inside) return;
+    collide_store<Q, S, HX, HY, H>(Lv, f, rho, u, tag, hself, s_rho, &s_u[0][0], tau, om, sigma, spsi, fdst, idx);
 }
 
 // ------------------------------------------------------------------ utilities
