@@ -113,6 +113,11 @@ struct LevelDev {
     int fast_lo[3], fast_hi[3];  // tile grown by 2 must stay in [fast_lo, fast_hi]
     int has_child;
     int child_lo[3], child_hi[3], child_per[3];  // closed child box in this level's box coordinates
+    // hanging nodes of this level: table rows [ie_base, ie_base + n_ie), TF stencils
+    int ie_base, n_ie;
+    const int *ie_nst;
+    const int *ie_st;
+    const double *ie_w;
 };
 
 __device__ __forceinline__ long long node_index(const LevelGeo &g, int x, int y, int z)

@@ -664,6 +664,13 @@ LevelDev level_dev(const lbm_h h, int l)
     d.tau = v.tau;
     tile_bounds(h, l, d.fast_lo, d.fast_hi, d.child_lo, d.child_hi, d.child_per);
     d.has_child = v.has_child ? 1 : 0;
+    d.ie_base = v.nTFP;
+    d.n_ie = v.nIE;
+    if (l > 0) {
+        d.ie_nst = h->ifc[l].dev.ie_nst;
+        d.ie_st = h->ifc[l].dev.ie_st;
+        d.ie_w = h->ifc[l].dev.ie_w;
+    }
     return d;
 }
 
@@ -731,23 +738,21 @@ struct Sched {
         // interface kernels: one 16- (D2Q9) or 32-lane (D3Q19) segment per node, 128 threads per block
         constexpr int SEG = 128 / (Q <= 16 ? 16 : 32);
         LevelDev dv = level_dev(h, l);
-        if (l + 1 < h->nl) {
-            const IfaceDev &I = h->ifc[l + 1].dev;
-            const int n = I.nTF + I.nRing;
-            if (n > 0) {
-                k_hist<Q, S><<<(n + SEG - 1) / SEG, 128, 0, h->stream>>>(I, dv.g, (const S *)fA, (int)((k + 1) % 3), 0);
-                h->launch_counter++;
-            }
-        }
+        // Newton at this level's TF nodes and the history push for the child interface
+        // are independent: one launch
+        const bool recon = l > 0 && h->ifc[l].dev.nTF > 0;
+        const bool hist = l + 1 < h->nl && h->ifc[l + 1].dev.nTF + h->ifc[l + 1].dev.nRing > 0;
         TimeW tw{};
-        if (l > 0) {
-            tw = weights(phase, kp);
-            const IfaceDev &I = h->ifc[l].dev;
-            if (I.nTF > 0) {
-                k_recon<Q, S><<<(I.nTF + SEG - 1) / SEG, 128, 0, h->stream>>>(
-                    I, dv, level_dev(h, l - 1), (const S *)fA, tw, phase, h->d_status, h->d_maxit);
-                h->launch_counter++;
-            }
+        if (l > 0) tw = weights(phase, kp);
+        if (recon || hist) {
+            const IfaceDev Ir = recon ? h->ifc[l].dev : IfaceDev{};
+            const IfaceDev Ih = hist ? h->ifc[l + 1].dev : IfaceDev{};
+            const int nbr = recon ? (Ir.nTF + SEG - 1) / SEG : 0;
+            const int nbh = hist ? (Ih.nTF + Ih.nRing + SEG - 1) / SEG : 0;
+            k_recon_hist<Q, S><<<nbr + nbh, 128, 0, h->stream>>>(Ir, dv, l > 0 ? level_dev(h, l - 1) : dv,
+                                                                (const S *)fA, tw, phase, h->d_status, h->d_maxit, nbr,
+                                                                Ih, dv.g, (const S *)fA, (int)((k + 1) % 3));
+            h->launch_counter++;
         }
         if (l + 1 < h->nl) {
             level_step(h, l + 1, 2 * k, 0, k);
@@ -755,13 +760,10 @@ struct Sched {
         }
         if (l > 0) {
             const IfaceDev &I = h->ifc[l].dev;
-            if (I.nTF > 0) {
-                k_grad<Q, S><<<(I.nTF + SEG - 1) / SEG, 128, 0, h->stream>>>(I, dv, level_dev(h, l - 1), (const S *)fA,
-                                                                            tw, phase);
-                h->launch_counter++;
-            }
-            if (I.nIE > 0) {
-                k_ie<Q, S><<<(I.nIE + SEG - 1) / SEG, 128, 0, h->stream>>>(I, dv, (const S *)fA);
+            const int nbg = (I.nTF + SEG - 1) / SEG, nbi = (I.nIE + SEG - 1) / SEG;
+            if (nbg + nbi > 0) {
+                k_grad_ie<Q, S><<<nbg + nbi, 128, 0, h->stream>>>(I, dv, level_dev(h, l - 1), (const S *)fA, tw, phase,
+                                                                  nbg);
                 h->launch_counter++;
             }
         }

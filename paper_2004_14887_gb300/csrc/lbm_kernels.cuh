@@ -230,7 +230,7 @@ __device__ int newton_seg(const int *c, T w, T fhat, T gam, T tol, bool active, 
 // the fine rebuild of gamma=c populations (Eq. rescff) and on sync sub-steps the
 // coarse rebuild of all populations (Eq. rescfc).  One W-lane segment per TF node.
 template <int Q, typename S>
-__global__ void __launch_bounds__(128) k_recon(IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict__ ff,
+__device__ __forceinline__ void recon_body(int bid, IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict__ ff,
                                                  TimeW tw, int sync, int *status, int *max_iters)
 {
     using L = Lat<Q>;
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(128) k_recon(IfaceDev I, LevelDev F, LevelDev 
     constexpr int D = L::D;
     constexpr int W = Q <= 16 ? 16 : 32;
     const int lane = threadIdx.x & 31;
-    const int seg = (blockIdx.x * blockDim.x + threadIdx.x) / W;
+    const int seg = (bid * blockDim.x + threadIdx.x) / W;
     const int i = lane % W;
     const bool live = seg < I.nTF;
     const int t = live ? seg : 0;
@@ -298,13 +298,13 @@ __global__ void __launch_bounds__(128) k_recon(IfaceDev I, LevelDev F, LevelDev 
 // macros at ring nodes, for the child level's Eq. (TempInt).  One W-lane segment
 // per node, lane i handles population i (TF segments first, then ring segments).
 template <int Q, typename S>
-__global__ void __launch_bounds__(128) k_hist(IfaceDev I, LevelGeo gc, const S *__restrict__ fc, int slot, int seed)
+__device__ __forceinline__ void hist_body(int bid, IfaceDev I, LevelGeo gc, const S *__restrict__ fc, int slot, int seed)
 {
     using L = Lat<Q>;
     using R = typename St<S>::R;
     constexpr int D = L::D;
     constexpr int W = Q <= 16 ? 16 : 32;
-    const int seg = (blockIdx.x * blockDim.x + threadIdx.x) / W;
+    const int seg = (bid * blockDim.x + threadIdx.x) / W;
     const int i = threadIdx.x % W;
     int c[3];
     double wd;
@@ -344,14 +344,14 @@ __global__ void __launch_bounds__(128) k_hist(IfaceDev I, LevelGeo gc, const S *
 // W-lane segment per TF node: the lanes pull the populations of fine neighbours in
 // parallel; every lane then holds the stencil and lanes 0..11 write S and C.
 template <int Q, typename S>
-__global__ void __launch_bounds__(128) k_grad(IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict__ ff,
+__device__ __forceinline__ void grad_body(int bid, IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict__ ff,
                                                 TimeW tw, int sync)
 {
     using L = Lat<Q>;
     using R = typename St<S>::R;
     constexpr int D = L::D;
     constexpr int W = Q <= 16 ? 16 : 32;
-    const int seg = (blockIdx.x * blockDim.x + threadIdx.x) / W;
+    const int seg = (bid * blockDim.x + threadIdx.x) / W;
     const int i = threadIdx.x % W;
     const bool live = seg < I.nTF;
     const int t = live ? seg : 0;
@@ -415,17 +415,17 @@ __global__ void __launch_bounds__(128) k_grad(IfaceDev I, LevelDev F, LevelDev C
 
 // ------------------------------------------------------------------ hanging nodes
 // 4-point 1-D Lagrange along the interface (tensor order over odd axes, one-sided
-// next to corners) of missing populations, S and C; macros are the moments.  One
-// W-lane segment per hanging node: lane i completes population i, lanes 0..11
-// interpolate the S and C components.
+// next to corners) of missing populations; macros are the moments.  One W-lane
+// segment per hanging node, lane i completes population i.  S and C of hanging
+// nodes are interpolated with the same stencil where they are used (collide_store).
 template <int Q, typename S>
-__global__ void __launch_bounds__(128) k_ie(IfaceDev I, LevelDev F, const S *__restrict__ ff)
+__device__ __forceinline__ void ie_body(int bid, IfaceDev I, LevelDev F, const S *__restrict__ ff)
 {
     using L = Lat<Q>;
     using R = typename St<S>::R;
     constexpr int D = L::D;
     constexpr int W = Q <= 16 ? 16 : 32;
-    const int seg = (blockIdx.x * blockDim.x + threadIdx.x) / W;
+    const int seg = (bid * blockDim.x + threadIdx.x) / W;
     const int i = threadIdx.x % W;
     const bool live = seg < I.nIE;
     const int e = live ? seg : 0;
@@ -446,18 +446,39 @@ __global__ void __launch_bounds__(128) k_ie(IfaceDev I, LevelDev F, const S *__r
         }
         fpop[(long long)i * nif + row] = v;
     }
-    if (live && i < 12) {
-        const int k = i % 6;
-        R *tab = (R *)(i < 6 ? F.if_S : F.if_C);
-        R acc = R(0);
-        for (int j = 0; j < nst; j++) acc += (R)I.ie_w[e * 16 + j] * tab[(long long)k * nif + I.ie_st[e * 16 + j]];
-        tab[(long long)k * nif + row] = acc;
-    }
     const R rho = seg_sum<W>(v);
     R m[3] = {R(0), R(0), R(0)};
 #pragma unroll
     for (int a = 0; a < D; a++) m[a] = seg_sum<W>(R(c[a]) * v);
     if (live && i < 4) ((R *)F.if_mac)[(long long)i * nif + row] = i == 0 ? rho : (i <= D ? m[i - 1] / rho : R(0));
+}
+
+
+// ------------------------------------------------------------------ fused launches
+// blocks [0, nb_a) run the first body, the rest the second: the two halves work on
+// independent data (a different interface, or TF nodes vs hanging nodes of the same
+// interface whose inputs were all written by earlier launches)
+template <int Q, typename S>
+__global__ void __launch_bounds__(128) k_recon_hist(IfaceDev Ir, LevelDev F, LevelDev Cl, const S *__restrict__ ff,
+                                                      TimeW tw, int sync, int *status, int *max_iters, int nb_recon,
+                                                      IfaceDev Ih, LevelGeo gh, const S *__restrict__ fh, int slot)
+{
+    if ((int)blockIdx.x < nb_recon) recon_body<Q, S>(blockIdx.x, Ir, F, Cl, ff, tw, sync, status, max_iters);
+    else hist_body<Q, S>(blockIdx.x - nb_recon, Ih, gh, fh, slot, 0);
+}
+
+template <int Q, typename S>
+__global__ void __launch_bounds__(128) k_hist(IfaceDev I, LevelGeo gc, const S *__restrict__ fc, int slot, int seed)
+{
+    hist_body<Q, S>(blockIdx.x, I, gc, fc, slot, seed);
+}
+
+template <int Q, typename S>
+__global__ void __launch_bounds__(128) k_grad_ie(IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict__ ff,
+                                                   TimeW tw, int sync, int nb_grad)
+{
+    if ((int)blockIdx.x < nb_grad) grad_body<Q, S>(blockIdx.x, I, F, Cl, ff, tw, sync);
+    else ie_body<Q, S>(blockIdx.x - nb_grad, I, F, ff);
 }
 
 // rho, u of the node at box coordinates (xx, yy, zz) for the shared-memory halo:
@@ -581,6 +602,24 @@ __device__ __forceinline__ void collide_store(const LevelDev &Lv, typename St<S>
                 if (D == 2) nu[b][s2][2] = R(0);
             }
         fd_gradients<D, R>(nr, nu, R(0.5), Sv, Cv);
+    } else if (tag >= Lv.ie_base && tag < Lv.ie_base + Lv.n_ie) {
+        // hanging node: S and C by the same 4-point stencil as its missing populations
+        const R *tS = (const R *)Lv.if_S, *tC = (const R *)Lv.if_C;
+        const int e = tag - Lv.ie_base, nst = Lv.ie_nst[e];
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            Sv[k] = R(0);
+            Cv[k] = R(0);
+        }
+        for (int j = 0; j < nst; j++) {
+            const int tf = Lv.ie_st[e * 16 + j];
+            const R wj = (R)Lv.ie_w[e * 16 + j];
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                Sv[k] += wj * tS[(long long)k * Lv.nif + tf];
+                Cv[k] += wj * tC[(long long)k * Lv.nif + tf];
+            }
+        }
     } else {
         const R *tS = (const R *)Lv.if_S, *tC = (const R *)Lv.if_C;
 #pragma unroll
