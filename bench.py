@@ -105,10 +105,29 @@ def _dist():
     return ws, rank, local
 
 
-def _traffic_from_profiles(kernel_key):
-    """DRAM bytes per launch recorded by an ncu capture in profiles/ for this kernel
-    and source revision, or None."""
-    path = os.path.join(ROOT, "profiles", "k_bulk_pulse2d_3lvl_f32.md")
+WORKLOAD_TEXT = {
+    "pulse2d_3lvl": "pulse2d_3lvl: D2Q9, 3 levels, coarse 512^2 periodic, patches 256^2 and 128^2 coarse cells, "
+                    "Mach 0.2, A=1e-3",
+    "vortex2d_2lvl": "vortex2d_2lvl: D2Q9, 2 levels, coarse 128^2 periodic, patch 64^2 coarse cells, vortex at Mach 0.1",
+    "vortex3d_3lvl": "vortex3d_3lvl: D3Q19, 3 levels, coarse 256^3 periodic, cubes 128^3 and 64^3 coarse cells, "
+                     "vortex tube + 1% noise at Mach 0.1",
+    "slab3d_3lvl": "slab3d_3lvl: D3Q19, 3 levels, coarse 512x512x256, slab z in [96,160) and box "
+                   "[128,384)^2 x [112,144), pulse 1e-4 + vortex at Mach 0.15",
+}
+DEFAULT_STORAGE = {"pulse2d_3lvl": "f32", "vortex2d_2lvl": "f64", "vortex3d_3lvl": "f32", "slab3d_3lvl": "f16s"}
+
+
+def _workloads():
+    from paper_2004_14887_gb300 import workloads as W
+
+    return {"pulse2d_3lvl": W.pulse2d, "vortex2d_2lvl": W.vortex2d, "vortex3d_3lvl": W.vortex3d,
+            "slab3d_3lvl": W.slab3d}
+
+
+def _traffic_from_profiles(workload, storage):
+    """DRAM bytes per launch recorded by an ncu capture in profiles/ for this kernel,
+    workload and kernel-source revision, or None."""
+    path = os.path.join(ROOT, "profiles", f"k_bulk_{workload}_{storage}.md")
     if not os.path.exists(path):
         return None
     try:
@@ -117,7 +136,7 @@ def _traffic_from_profiles(kernel_key):
         import hashlib
 
         h = hashlib.sha1()
-        for s in B.sources() + [os.path.join(B.CSRC, "lbm_kernels.cuh"), os.path.join(B.CSRC, "lbm_device.cuh")]:
+        for s in [os.path.join(B.CSRC, "lbm_kernels.cuh"), os.path.join(B.CSRC, "lbm_device.cuh")]:
             h.update(open(s, "rb").read())
         sha = h.hexdigest()[:12]
         txt = open(path).read()
@@ -136,6 +155,7 @@ def run_gb300(args):
     from paper_2004_14887_gb300 import lbm
     from paper_2004_14887_gb300 import workloads as W
 
+    WORKLOADS = _workloads()
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     # one non-default stream for the library, the L2 flushes and the timing events
@@ -163,8 +183,11 @@ def run_gb300(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
 
     def make(storage, use_graphs=True):
-        d = W.pulse2d(storage=storage)
+        d = WORKLOADS[args.workload](storage=storage)
+        tc = time.perf_counter()
         h = lbm.Hierarchy(d, use_graphs=use_graphs)
+        print(f"[bench] {args.workload} {storage}: set-up {time.perf_counter() - tc:.2f} s, "
+              f"{h.device_bytes() / 1e9:.2f} GB on the device", file=sys.stderr, flush=True)
         for l in range(h.n_levels):
             r, u = W.init_fields(d, l)
             h.init_fields(l, r, u)
@@ -203,7 +226,8 @@ def run_gb300(args):
         return dev_ms, wall, h.launch_count() - n0, clocks
 
     K, Wm = args.steps, args.warmup
-    d, h = make("f32")
+    main_storage = args.storage or DEFAULT_STORAGE[args.workload]
+    d, h = make(main_storage)
     upd = W.updates_per_coarse_step(d)
     feq = W.fine_equivalent_per_coarse_step(d)
     dev_ms, wall, launches, clocks = timed(h, K, Wm, sampler_dev=local)
@@ -222,16 +246,16 @@ def run_gb300(args):
     h.timing_enable(False)
     bulk_ms = [m / max(c, 1) for m, c in zip(ms, cnt)]
     nact = [h.levels[l]["n_active"] for l in range(L)]
-    bytes_finest = nact[L - 1] * 2 * h.q * BYTES_PER_POP["f32"]
+    bytes_finest = nact[L - 1] * 2 * h.q * BYTES_PER_POP[main_storage]
     peak, peak_src = _peaks()
     achieved = bytes_finest / (bulk_ms[L - 1] * 1e-3) / 1e9
 
     # reduced / full precision variants on the same workload
     variants = {}
     if not args.no_variants:
-        for st in ("f64", "f16s"):
+        for st in [x for x in ("f64", "f32", "f16s") if x != main_storage]:
             dv, hv = make(st)
-            Kv = min(K, 400 if st == "f64" else K)
+            Kv = min(K, args.variant_steps if st == "f64" else K)
             dms, _, _, _ = timed(hv, Kv, max(3, Wm // 2))
             tv = max_over_ranks(dms) / 1e3
             hv.timing_enable(True)
@@ -248,13 +272,16 @@ def run_gb300(args):
             }
             hv.close()
             del hv
-        variants["f32_speedup_vs_f64"] = value / variants["f64"]["value"]
-        variants["f16s_speedup_vs_f64"] = variants["f16s"]["value"] / variants["f64"]["value"]
+        vals = dict(variants)
+        vals[main_storage] = {"value": value}
+        for st in ("f32", "f16s"):
+            if st in vals and "f64" in vals:
+                variants[f"{st}_speedup_vs_f64"] = vals[st]["value"] / vals["f64"]["value"]
 
     # end to end through the public API with host buffers: init (H2D), K steps, macros (D2H)
     e2e = None
     if not args.no_e2e:
-        de = W.pulse2d(storage="f32")
+        de = WORKLOADS[args.workload](storage=main_storage)
         he = lbm.Hierarchy(de)
         fields = []
         for l in range(he.n_levels):
@@ -286,19 +313,19 @@ def run_gb300(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
         "ms_per_step": 1e3 * t / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic (seeded analytic pulse, no dataset)",
-        "config": {"workload": "pulse2d_3lvl: D2Q9, 3 levels, coarse 512^2 periodic, patches 256^2 and 128^2 "
-                               "coarse cells, Mach 0.2, A=1e-3, FP32 storage", "levels": L,
+        "dtype": main_storage, "data": "synthetic (seeded analytic fields, no dataset)",
+        "config": {"workload": WORKLOAD_TEXT[args.workload] + f", {main_storage} storage", "levels": L,
                    "node_updates_per_step": upd, "fine_equivalent_updates_per_step": feq,
                    "active_nodes_per_level": nact, "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
         "actual_mlups": actual,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": _traffic_from_profiles("k_bulk"), "kernel": "k_bulk<9,float> level 2",
+                     "traffic": _traffic_from_profiles(args.workload, main_storage),
+                     "kernel": f"bulk collide-and-stream, finest level (level {L - 1})",
                      "algorithmic_bytes_per_launch": bytes_finest, "avg_launch_ms": bulk_ms[L - 1],
                      "peak_source": f"{peak_src} hbm_gbs"},
         "bulk_ms_per_launch_by_level": bulk_ms,
-        "step_roofline_frac": (upd * 2 * h.q * 4) / (t / K) / 1e9 / peak,
+        "step_roofline_frac": (upd * 2 * h.q * BYTES_PER_POP[main_storage]) / (t / K) / 1e9 / peak,
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": e2e,
@@ -379,6 +406,9 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="pulse2d_3lvl", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--storage", default=None, choices=["f64", "f32", "f16s"])
+    ap.add_argument("--variant-steps", type=int, default=400)
     ap.add_argument("--cpu-steps", type=int, default=150)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
