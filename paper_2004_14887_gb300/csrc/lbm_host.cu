@@ -468,7 +468,7 @@ int build_interfaces(lbm_h h)
 
 constexpr int T2X = 32, T2YT = 8, T2NR = 2;  // D2Q9 tile: 32 x 8 threads, 2 rows per thread
 constexpr int T2Y = T2YT * T2NR;
-constexpr int T3X = 32, T3Y = 4, T3Z = 2;    // D3Q19 tile
+constexpr int T3X = 32, T3Y = 8, T3Z = 32;   // D3Q19: 32 x 8 column, 32-plane z chunk (z-marching)
 
 void build_tiles(lbm_h h)
 {
@@ -478,6 +478,7 @@ void build_tiles(lbm_h h)
         v.tiles[0] = (int)((v.n[0] + TX - 1) / TX);
         v.tiles[1] = (int)((v.n[1] + TY - 1) / TY);
         v.tiles[2] = (int)((v.n[2] + TZ - 1) / TZ);
+        if (h->D == 3) continue;  // 3-D columns are classified plane by plane (check_planes)
         const long long nt = (long long)v.tiles[0] * v.tiles[1] * v.tiles[2];
         v.tile_flag.assign(nt, TILE_GENERAL);
         const int rz = h->D == 3 ? 2 : 0;
@@ -540,10 +541,64 @@ unsigned char geometric_class(const lbm_h h, int l, const int *t0, const int *T)
     return fast ? TILE_FAST : TILE_GENERAL;
 }
 
+// 3-D: the kernel's per-plane rule (plane_class), replayed on the host
+int geometric_plane_class(const lbm_h h, int l, int X0, int Y0, int TX, int TY, int p)
+{
+    const Level &v = h->lev[l];
+    int flo[3], fhi[3], clo[3], chi[3], cper[3];
+    tile_bounds(h, l, flo, fhi, clo, chi, cper);
+    const int lo[3] = {X0 - 2, Y0 - 2, p - 1}, hi[3] = {X0 + TX + 1, Y0 + TY + 1, p + 1};
+    bool fast = true;
+    for (int a = 0; a < 3; a++)
+        if (lo[a] < flo[a] || hi[a] > fhi[a]) fast = false;
+    if (v.has_child) {
+        bool disjoint = false, in_hole = true;
+        const int hlo[3] = {X0 - 1, Y0 - 1, p};
+        const int hhi[3] = {std::min<int>(X0 + TX, (int)v.n[0] - 1), std::min<int>(Y0 + TY, (int)v.n[1] - 1), p};
+        for (int a = 0; a < 3; a++) {
+            if (cper[a]) continue;
+            if (hi[a] < clo[a] || lo[a] > chi[a]) disjoint = true;
+            if (!(hlo[a] > clo[a] && hhi[a] < chi[a])) in_hole = false;
+        }
+        if (in_hole) return 1;
+        if (!disjoint) fast = false;
+    }
+    return fast ? 0 : 2;
+}
+
+// every (column, plane) of a 3-D level: a fast plane must only meet bulk nodes, a hole
+// plane only hole nodes (general planes are correct for any classification)
+int check_planes(lbm_h h)
+{
+    for (int l = 0; l < h->nl; l++) {
+        const Level &v = h->lev[l];
+        const int tx = (int)((v.n[0] + T3X - 1) / T3X), ty = (int)((v.n[1] + T3Y - 1) / T3Y);
+        for (int by = 0; by < ty; by++)
+            for (int bx = 0; bx < tx; bx++)
+                for (int p = 0; p < (int)v.n[2]; p++) {
+                    const int X0 = bx * T3X, Y0 = by * T3Y;
+                    const int cls = geometric_plane_class(h, l, X0, Y0, T3X, T3Y, p);
+                    if (cls == 2) continue;
+                    const int r = cls == 0 ? 2 : 1, rz = cls == 0 ? 1 : 0;
+                    for (int z = p - rz; z <= p + rz; z++)
+                        for (int y = Y0 - r; y < Y0 + T3Y + r; y++)
+                            for (int x = X0 - r; x < X0 + T3X + r; x++) {
+                                const bool in = x >= 0 && y >= 0 && z >= 0 && x < v.n[0] && y < v.n[1] && z < v.n[2];
+                                if (cls == 0 && (!in || v.cls[x + v.n[0] * (y + v.n[1] * (long long)z)] != LBM_NODE_BULK))
+                                    return fail(nullptr, LBM_ERR_BAD_DESC, "internal: fast plane %d of level %d meets a non-bulk node", p, l);
+                                if (cls == 1 && in && v.cls[x + v.n[0] * (y + v.n[1] * (long long)z)] != LBM_NODE_HOLE)
+                                    return fail(nullptr, LBM_ERR_BAD_DESC, "internal: hole plane %d of level %d meets a node", p, l);
+                            }
+                }
+    }
+    return LBM_OK;
+}
+
 // every tile: the geometric rule must agree with the node-by-node classification
 int check_tiles(lbm_h h)
 {
-    const int TX = h->D == 2 ? T2X : T3X, TY = h->D == 2 ? T2Y : T3Y, TZ = h->D == 2 ? 1 : T3Z;
+    if (h->D == 3) return check_planes(h);
+    const int TX = T2X, TY = T2Y, TZ = 1;
     const int T[3] = {TX, TY, TZ};
     for (int l = 0; l < h->nl; l++) {
         const Level &v = h->lev[l];
@@ -698,8 +753,8 @@ struct Sched {
             k_bulk2d<Q, S, T2X, T2YT, T2NR><<<nt, T2X * T2YT, 0, h->stream>>>(level_dev(h, l), (const S *)src,
                                                                              (S *)dst, tau, om, sig, sps);
         else
-            k_bulk<Q, S, T3X, T3Y, T3Z><<<nt, T3X * T3Y * T3Z, 0, h->stream>>>(level_dev(h, l), (const S *)src,
-                                                                              (S *)dst, tau, om, sig, sps);
+            k_bulk3d<Q, S, T3X, T3Y, T3Z><<<nt, T3X * T3Y, 0, h->stream>>>(level_dev(h, l), (const S *)src, (S *)dst,
+                                                                          tau, om, sig, sps);
         h->launch_counter++;
         if (h->timing) {
             cudaEventRecord(h->ev_pool[ev + 1], h->stream);

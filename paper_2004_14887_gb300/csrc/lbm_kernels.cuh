@@ -481,52 +481,6 @@ __global__ void __launch_bounds__(128) k_grad_ie(IfaceDev I, LevelDev F, LevelDe
     else ie_body<Q, S>(blockIdx.x - nb_grad, I, F, ff);
 }
 
-// rho, u of the node at box coordinates (xx, yy, zz) for the shared-memory halo:
-// wraps periodic axes, pulls bulk nodes, reads interface nodes from the table;
-// returns false (and rho = 1, u = 0) off a non-periodic box or in the hole.
-template <int Q, typename S>
-__device__ __forceinline__ bool halo_macros(const LevelDev &Lv, const S *__restrict__ fsrc, int xx, int yy, int zz,
-                                            typename St<S>::R &hr, typename St<S>::R *hu)
-{
-    using L = Lat<Q>;
-    using R = typename St<S>::R;
-    constexpr int D = L::D;
-    const LevelGeo &g = Lv.g;
-    hr = R(1);
-    hu[0] = hu[1] = hu[2] = R(0);
-    if (!(wrap_coord(xx, g.n[0], g.per[0]) && wrap_coord(yy, g.n[1], g.per[1]) && wrap_coord(zz, g.n[2], g.per[2])))
-        return false;
-    const long long hidx = node_index(g, xx, yy, zz);
-    const int htag = Lv.tag[hidx];
-    if (htag == TAG_BULK) {
-        R m[3] = {R(0), R(0), R(0)};
-        hr = R(0);
-#pragma unroll
-        for (int i = 0; i < Q; i++) {
-            int sx = xx - L::c(i, 0), sy = yy - L::c(i, 1), sz = zz - L::c(i, 2);
-            if (!wrap_coord(sx, g.n[0], g.per[0])) sx = xx;  // bulk sources are nodes: never taken
-            if (!wrap_coord(sy, g.n[1], g.per[1])) sy = yy;
-            if (!wrap_coord(sz, g.n[2], g.per[2])) sz = zz;
-            const R v = St<S>::ld(fsrc, (long long)i * g.pitch + node_index(g, sx, sy, sz), L::w(i));
-            hr += v;
-#pragma unroll
-            for (int a = 0; a < D; a++)
-                if (L::c(i, a) != 0) m[a] += R(L::c(i, a)) * v;
-        }
-#pragma unroll
-        for (int a = 0; a < D; a++) hu[a] = m[a] / hr;
-        return true;
-    }
-    if (htag >= 0) {
-        const R *mac = (const R *)Lv.if_mac;
-        hr = mac[htag];
-#pragma unroll
-        for (int a = 0; a < D; a++) hu[a] = mac[(long long)(1 + a) * Lv.nif + htag];
-        return true;
-    }
-    return false;
-}
-
 // ------------------------------------------------------------------ bulk collide-and-stream
 // Tile class from the box geometry alone (no memory access): FAST when the tile
 // grown by two nodes stays inside the band of bulk nodes (off the level's own outline,
@@ -793,104 +747,233 @@ __global__ void __launch_bounds__(TX *TYT) k_bulk2d(LevelDev Lv, const S *__rest
     }
 }
 
-// 3-D: one CTA per tile of TX x TY x TZ nodes, one node per thread.
-template <int Q, typename S, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(TX *TY *TZ) k_bulk(LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
-                                                      typename St<S>::R tau, typename St<S>::R om,
-                                                      typename St<S>::R sigma, typename St<S>::R spsi)
+// Geometric class of one plane p of a z-marching tile: LOAD_FAST when the tile grown by
+// two nodes in x and y, over planes p-1..p+1, lies in the band of bulk nodes (its own
+// nodes and their halo are bulk, all their sources are nodes without periodic wrap);
+// LOAD_HOLE when the tile grown by one node in x and y lies strictly inside the child
+// box at plane p (nothing to load); LOAD_GENERAL otherwise.
+enum : int { LOAD_FAST = 0, LOAD_HOLE = 1, LOAD_GENERAL = 2 };
+
+__device__ __forceinline__ int plane_class(const LevelDev &Lv, int X0, int Y0, int TX, int TY, int p)
+{
+    const int lo[3] = {X0 - 2, Y0 - 2, p - 1}, hi[3] = {X0 + TX + 1, Y0 + TY + 1, p + 1};
+    bool fast = true;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        if (lo[a] < Lv.fast_lo[a] || hi[a] > Lv.fast_hi[a]) fast = false;
+    if (Lv.has_child) {
+        bool disjoint = false, in_hole = true;
+        const int hlo[3] = {X0 - 1, Y0 - 1, p}, hhi[3] = {min(X0 + TX, Lv.g.n[0] - 1), min(Y0 + TY, Lv.g.n[1] - 1), p};
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            if (Lv.child_per[a]) continue;
+            if (hi[a] < Lv.child_lo[a] || lo[a] > Lv.child_hi[a]) disjoint = true;
+            if (!(hlo[a] > Lv.child_lo[a] && hhi[a] < Lv.child_hi[a])) in_hole = false;
+        }
+        if (in_hole) return LOAD_HOLE;
+        if (!disjoint) fast = false;
+    }
+    return fast ? LOAD_FAST : LOAD_GENERAL;
+}
+
+// populations (pull) and tag of the node at box coordinates (x, y, z) of a general plane:
+// periodic positions wrap; interface nodes read the table; holes and positions off a
+// non-periodic box give tag TAG_HOLE
+template <int Q, typename S>
+__device__ __forceinline__ int general_pull(const LevelDev &Lv, const S *__restrict__ fsrc, int x, int y, int z,
+                                            typename St<S>::R (&f)[Q])
 {
     using L = Lat<Q>;
     using R = typename St<S>::R;
-    constexpr int D = L::D;
-    static_assert(D == 3, "3-D kernel");
-    constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
-    constexpr int H = HX * HY * HZ;
-    constexpr int NT = TX * TY * TZ;
-    __shared__ R s_rho[H];
-    __shared__ R s_u[D][H];
+    const LevelGeo &g = Lv.g;
+    const bool ok = wrap_coord(x, g.n[0], g.per[0]) && wrap_coord(y, g.n[1], g.per[1]) && wrap_coord(z, g.n[2], g.per[2]);
+    const int tag = ok ? Lv.tag[box_index(g, x, y, z)] : TAG_HOLE;
+    const R *pop = (const R *)Lv.if_pop;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        // bulk sources are nodes: a one-step wrap on periodic axes is all they need
+        int sx = x - L::c(i, 0), sy = y - L::c(i, 1), sz = z - L::c(i, 2);
+        sx += (sx < 0) ? g.n[0] : ((sx >= g.n[0]) ? -g.n[0] : 0);
+        sy += (sy < 0) ? g.n[1] : ((sy >= g.n[1]) ? -g.n[1] : 0);
+        sz += (sz < 0) ? g.n[2] : ((sz >= g.n[2]) ? -g.n[2] : 0);
+        f[i] = tag == TAG_BULK ? St<S>::ld(fsrc + (long long)i * g.pitch, box_index(g, sx, sy, sz), L::w(i))
+                               : (tag >= 0 ? pop[(long long)i * Lv.nif + tag] : R(0));
+    }
+    return tag;
+}
+
+template <int Q, typename R>
+__device__ __forceinline__ void tag_macros(const LevelDev &Lv, int tag, const R (&f)[Q], R &rho, R *u)
+{
+    constexpr int D = Lat<Q>::D;
+    rho = R(1);
+    u[0] = u[1] = u[2] = R(0);
+    if (tag == TAG_BULK) {
+        reg_moments<Q, R>(f, rho, u);
+    } else if (tag >= 0) {
+        const R *mac = (const R *)Lv.if_mac;
+        rho = mac[tag];
+#pragma unroll
+        for (int a = 0; a < D; a++) u[a] = mac[(long long)(1 + a) * Lv.nif + tag];
+    }
+}
+
+// 3-D z-marching bulk kernel: one CTA per TX x TY column of nodes and chunk of ZC
+// planes.  The CTA keeps the macros of planes z-1, z, z+1 (tile + one-node x-y halo)
+// in a 3-plane shared ring and the post-stream populations of its own nodes of plane z
+// in registers; each step pulls plane z+1 (own nodes and the 2(TX+TY)+4 halo nodes,
+// one per thread), then collides plane z.  The z halo is reused, so a node is pulled
+// 1 + (halo share) times instead of the 3-D tile's (TX+2)(TY+2)(TZ+2)/(TX TY TZ).
+template <int Q, typename S, int TX, int TY, int ZC>
+__global__ void __launch_bounds__(TX *TY) k_bulk3d(LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
+                                                    typename St<S>::R tau, typename St<S>::R om,
+                                                    typename St<S>::R sigma, typename St<S>::R spsi)
+{
+    using L = Lat<Q>;
+    using R = typename St<S>::R;
+    constexpr int D = 3;
+    static_assert(L::D == 3, "3-D kernel");
+    constexpr int HX = TX + 2, HY = TY + 2, HP = HX * HY;
+    constexpr int NT = TX * TY;
+    constexpr int NB = 2 * HX + 2 * TY;
+    static_assert(NB <= NT, "one halo column per thread at most");
+    __shared__ R s_rho[3][HP];
+    __shared__ R s_u[3][3][HP];
 
     const LevelGeo &g = Lv.g;
-    const int X0 = blockIdx.x * TX, Y0 = blockIdx.y * TY, Z0 = blockIdx.z * TZ;
-    const int t0[3] = {X0, Y0, Z0}, T[3] = {TX, TY, TZ};
-    const unsigned char flag = tile_class<D>(Lv, t0, T);
-    if (flag == TILE_SKIP) return;
+    const int X0 = blockIdx.x * TX, Y0 = blockIdx.y * TY;
+    const int zb = blockIdx.z * ZC, ze = min(zb + ZC, g.n[2]);
     const int tid = threadIdx.x;
-    const int tx = tid % TX, ty = (tid / TX) % TY, tz = tid / (TX * TY);
-    const int x = X0 + tx, y = Y0 + ty, z = Z0 + tz;
-    const int n01 = g.n[0] * g.n[1];  // boxes hold fewer than 2^31 nodes
-    const bool inside = x < g.n[0] && y < g.n[1] && z < g.n[2];
-    const int idx = x + g.n[0] * y + n01 * z;
-    const int hself = (tx + 1) + HX * ((ty + 1) + HY * (tz + 1));
-
-    R f[Q];
-    R rho = R(1), u[3] = {R(0), R(0), R(0)};
-    int tag = TAG_HOLE;
-    if (flag == TILE_FAST) {
-        tag = TAG_BULK;
-#pragma unroll
-        for (int i = 0; i < Q; i++) {
-            const int off = L::c(i, 0) + g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
-            f[i] = St<S>::ld(fsrc + (long long)i * g.pitch, idx - off, L::w(i));
+    const int tx = tid % TX, ty = tid / TX;
+    const int x = X0 + tx, y = Y0 + ty;
+    const bool in_xy = x < g.n[0] && y < g.n[1];
+    const int hs = (tx + 1) + HX * (ty + 1);
+    int hb = -1, hx = 0, hy = 0;
+    if (tid < NB) {
+        if (tid < HX) {
+            hx = tid;
+            hy = 0;
+        } else if (tid < 2 * HX) {
+            hx = tid - HX;
+            hy = HY - 1;
+        } else {
+            const int b = tid - 2 * HX;
+            hy = 1 + (b >> 1);
+            hx = (b & 1) ? HX - 1 : 0;
         }
-        reg_moments<Q, R>(f, rho, u);
-    } else if (inside) {
-        tag = Lv.tag[idx];
-        if (tag == TAG_BULK) {
-#pragma unroll
-            for (int i = 0; i < Q; i++) {
-                int sx = x - L::c(i, 0), sy = y - L::c(i, 1), sz = z - L::c(i, 2);
-                if (!wrap_coord(sx, g.n[0], g.per[0])) sx = x;  // bulk sources are nodes: never taken
-                if (!wrap_coord(sy, g.n[1], g.per[1])) sy = y;
-                if (!wrap_coord(sz, g.n[2], g.per[2])) sz = z;
-                f[i] = St<S>::ld(fsrc + (long long)i * g.pitch, node_index(g, sx, sy, sz), L::w(i));
-            }
-            reg_moments<Q, R>(f, rho, u);
-        } else if (tag >= 0) {
-            const R *pop = (const R *)Lv.if_pop;
-            const R *mac = (const R *)Lv.if_mac;
-#pragma unroll
-            for (int i = 0; i < Q; i++) f[i] = pop[(long long)i * Lv.nif + tag];
-            rho = mac[tag];
-#pragma unroll
-            for (int a = 0; a < D; a++) u[a] = mac[(long long)(1 + a) * Lv.nif + tag];
-        }
-    } else {
-        // a ragged last tile: on a periodic axis this position is the wrapped node
-        R hr, hu[3];
-        halo_macros<Q, S>(Lv, fsrc, x, y, z, hr, hu);
-        rho = hr;
-#pragma unroll
-        for (int a = 0; a < D; a++) u[a] = hu[a];
+        hb = hx + HX * hy;
     }
-    // halo ring
-    for (int h = tid; h < H; h += NT) {
-        const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
-        const bool border = hx == 0 || hx == HX - 1 || hy == 0 || hy == HY - 1 || hz == 0 || hz == HZ - 1;
-        if (!border) continue;
-        const int xx = X0 + hx - 1, yy = Y0 + hy - 1, zz = Z0 + hz - 1;
-        R hr = R(1), hu[3] = {R(0), R(0), R(0)};
-        if (flag == TILE_FAST) {
-            const int hidx = xx + g.n[0] * yy + n01 * zz;
-            R fh[Q];
+    const int qx = X0 + hx - 1, qy = Y0 + hy - 1;
+    const int n01 = g.n[0] * g.n[1];
+
+    // pull plane p into (f, tag) for the own node and the macros of own and halo nodes
+    // into ring slot p mod 3
+    auto load_plane = [&](int p, R (&f)[Q], int &tag) {
+        const int cls = plane_class(Lv, X0, Y0, TX, TY, p);
+        R fh[Q];
+        int htag = TAG_HOLE;
+        tag = TAG_HOLE;
+        if (cls == LOAD_FAST) {
+            tag = TAG_BULK;
+            htag = hb >= 0 ? TAG_BULK : TAG_HOLE;
+            const int idx = x + g.n[0] * y + n01 * p, hidx = qx + g.n[0] * qy + n01 * p;
 #pragma unroll
             for (int i = 0; i < Q; i++) {
                 const int off = L::c(i, 0) + g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
-                fh[i] = St<S>::ld(fsrc + (long long)i * g.pitch, hidx - off, L::w(i));
+                f[i] = St<S>::ld(fsrc + (long long)i * g.pitch, idx - off, L::w(i));
             }
-            reg_moments<Q, R>(fh, hr, hu);
-        } else {
-            halo_macros<Q, S>(Lv, fsrc, xx, yy, zz, hr, hu);
+            if (hb >= 0) {
+#pragma unroll
+                for (int i = 0; i < Q; i++) {
+                    const int off = L::c(i, 0) + g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
+                    fh[i] = St<S>::ld(fsrc + (long long)i * g.pitch, hidx - off, L::w(i));
+                }
+            }
+        } else if (cls == LOAD_GENERAL) {
+            tag = general_pull<Q, S>(Lv, fsrc, x, y, p, f);
+            if (hb >= 0) htag = general_pull<Q, S>(Lv, fsrc, qx, qy, p, fh);
         }
-        s_rho[h] = hr;
+        const int slot = ((p % 3) + 3) % 3;  // p may be -1 (periodic z)
+        R r, u[3];
+        tag_macros<Q, R>(Lv, tag, f, r, u);
+        s_rho[slot][hs] = r;
 #pragma unroll
-        for (int a = 0; a < D; a++) s_u[a][h] = hu[a];
+        for (int a = 0; a < D; a++) s_u[slot][a][hs] = u[a];
+        if (hb >= 0) {
+            tag_macros<Q, R>(Lv, htag, fh, r, u);
+            s_rho[slot][hb] = r;
+#pragma unroll
+            for (int a = 0; a < D; a++) s_u[slot][a][hb] = u[a];
+        }
+        if (!in_xy) tag = TAG_HOLE;  // a position past a periodic seam only feeds the halo
+    };
+
+    R fc[Q], fn[Q];
+    int tc, tn;
+    if (zb >= ze) return;
+    // prologue: planes zb-1 (macros only) and zb (kept in registers); on a
+    // non-periodic z axis plane -1 does not exist and plane 0 is never bulk
+    load_plane(zb - 1 >= 0 || g.per[2] ? zb - 1 : zb, fn, tn);
+    load_plane(zb, fc, tc);
+    for (int z = zb; z < ze; z++) {
+        load_plane(z + 1 < g.n[2] || g.per[2] ? z + 1 : z, fn, tn);
+        __syncthreads();
+        if (tc != TAG_HOLE) {
+            const int sm = (z + 2) % 3, s0 = z % 3, sp = (z + 1) % 3;  // planes z-1, z, z+1
+            R Sv[6], Cv[6];
+            const int idx = x + g.n[0] * y + n01 * z;
+            if (tc == TAG_BULK) {
+                R nr[3][2], nu[3][2][3];
+                const int hh[2][2] = {{hs + 1, hs - 1}, {hs + HX, hs - HX}};
+#pragma unroll
+                for (int b = 0; b < 2; b++)
+#pragma unroll
+                    for (int s2 = 0; s2 < 2; s2++) {
+                        nr[b][s2] = s_rho[s0][hh[b][s2]];
+#pragma unroll
+                        for (int a = 0; a < 3; a++) nu[b][s2][a] = s_u[s0][a][hh[b][s2]];
+                    }
+                nr[2][0] = s_rho[sp][hs];
+                nr[2][1] = s_rho[sm][hs];
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    nu[2][0][a] = s_u[sp][a][hs];
+                    nu[2][1][a] = s_u[sm][a][hs];
+                }
+                fd_gradients<D, R>(nr, nu, R(0.5), Sv, Cv);
+            } else {
+                const R *tS = (const R *)Lv.if_S, *tC = (const R *)Lv.if_C;
+                if (tc >= Lv.ie_base && tc < Lv.ie_base + Lv.n_ie) {
+                    const int e = tc - Lv.ie_base, nst = Lv.ie_nst[e];
+#pragma unroll
+                    for (int k = 0; k < 6; k++) Sv[k] = Cv[k] = R(0);
+                    for (int j = 0; j < nst; j++) {
+                        const int tf = Lv.ie_st[e * 16 + j];
+                        const R wj = (R)Lv.ie_w[e * 16 + j];
+#pragma unroll
+                        for (int k = 0; k < 6; k++) {
+                            Sv[k] += wj * tS[(long long)k * Lv.nif + tf];
+                            Cv[k] += wj * tC[(long long)k * Lv.nif + tf];
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 6; k++) {
+                        Sv[k] = tS[(long long)k * Lv.nif + tc];
+                        Cv[k] = tC[(long long)k * Lv.nif + tc];
+                    }
+                }
+            }
+            R rho = s_rho[s0][hs], u[3] = {s_u[s0][0][hs], s_u[s0][1][hs], s_u[s0][2][hs]};
+            hrr_collide<Q, R>(fc, rho, u, Sv, Cv, tau, om, sigma, spsi);
+#pragma unroll
+            for (int i = 0; i < Q; i++) St<S>::st(fdst + (long long)i * g.pitch, idx, fc[i], L::w(i));
+        }
+#pragma unroll
+        for (int i = 0; i < Q; i++) fc[i] = fn[i];
+        tc = tn;
+        __syncthreads();
     }
-    s_rho[hself] = rho;
-#pragma unroll
-    for (int a = 0; a < D; a++) s_u[a][hself] = u[a];
-    __syncthreads();
-    if (tag == TAG_HOLE || !inside) return;
-    collide_store<Q, S, HX, HY, H>(Lv, f, rho, u, tag, hself, s_rho, &s_u[0][0], tau, om, sigma, spsi, fdst, idx);
 }
 
 // ------------------------------------------------------------------ utilities
