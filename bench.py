@@ -113,15 +113,19 @@ WORKLOAD_TEXT = {
                      "vortex tube + 1% noise at Mach 0.1",
     "slab3d_3lvl": "slab3d_3lvl: D3Q19, 3 levels, coarse 512x512x256, slab z in [96,160) and box "
                    "[128,384)^2 x [112,144), pulse 1e-4 + vortex at Mach 0.15",
+    "vortex3d_3lvl_128": "vortex3d_3lvl_128: D3Q19, 3 levels, coarse 128^3 periodic, cubes 64^3 and 32^3 coarse "
+                         "cells (half-size replica of vortex3d_3lvl, for profiling)",
 }
-DEFAULT_STORAGE = {"pulse2d_3lvl": "f32", "vortex2d_2lvl": "f64", "vortex3d_3lvl": "f32", "slab3d_3lvl": "f16s"}
+DEFAULT_STORAGE = {"pulse2d_3lvl": "f32", "vortex2d_2lvl": "f64", "vortex3d_3lvl": "f32", "slab3d_3lvl": "f16s",
+                   "vortex3d_3lvl_128": "f32"}
 
 
 def _workloads():
     from paper_2004_14887_gb300 import workloads as W
 
     return {"pulse2d_3lvl": W.pulse2d, "vortex2d_2lvl": W.vortex2d, "vortex3d_3lvl": W.vortex3d,
-            "slab3d_3lvl": W.slab3d}
+            "slab3d_3lvl": W.slab3d,
+            "vortex3d_3lvl_128": lambda **kw: W.vortex3d(n=128, boxes=((32, 96), (48, 80)), **kw)}
 
 
 def _traffic_from_profiles(workload, storage):
