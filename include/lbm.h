@@ -161,8 +161,29 @@ LBM_API int lbm_reduce(lbm_h h, int level, double out[4]);
 #define LBM_STATIC_REDUCE_PARTIALS 4096
 LBM_API int lbm_reduce_static(lbm_h h, int level, double out[4]);
 
+/* Batches of independent hierarchies (cfg. "many hierarchies of uneven sizes"):
+ * lbm_create_batch builds n D2Q9 hierarchies with the same storage and level count
+ * on one stream; lbm_advance on the batch advances all of them together in ONE
+ * cooperative persistent launch per call: every phase of the sub-cycle schedule of
+ * Sec. 3.5 (history + Newton, gradients + hanging nodes, bulk) is one grid-stride
+ * pass over the work of all members, with a grid barrier between dependent phases.
+ * A barrier wait longer than 2 s gives up and the launch ends with LBM_ERR_TIMEOUT
+ * (read by lbm_check_status).  lbm_batch_member returns member i's handle, owned by
+ * the batch, for lbm_init_fields / lbm_get_macros / lbm_reduce / lbm_query_level;
+ * lbm_advance on a member is an error.  Members must be initialised together (the
+ * batch advances only when all members are at the same step).  lbm_destroy on the
+ * batch destroys its members. */
+LBM_API int lbm_create_batch(const lbm_hierarchy_desc *descs, int n, void *cuda_stream, lbm_h *out);
+LBM_API int lbm_batch_member(lbm_h batch, int i, lbm_h *member);
+/* Runs the batch's grid barrier alone over one block per SM; block skip_block (if >= 0)
+ * leaves without arriving, so the other blocks' waits run out after limit_us
+ * microseconds: returns LBM_ERR_TIMEOUT then, LBM_OK when skip_block < 0.  The
+ * device context stays usable either way.  Synchronises the batch's stream. */
+LBM_API int lbm_batch_check_barrier(lbm_h batch, int skip_block, int64_t limit_us);
+
 /* Device status word accumulated by the kernels since the last call (cleared on read):
- * returns LBM_OK, LBM_ERR_NEWTON or LBM_ERR_DIVERGED.  Synchronises the stream. */
+ * returns LBM_OK, LBM_ERR_TIMEOUT, LBM_ERR_NEWTON or LBM_ERR_DIVERGED.  Synchronises
+ * the stream. */
 LBM_API int lbm_check_status(lbm_h h);
 /* Largest Newton iteration count met since creation. */
 LBM_API int lbm_max_newton_iters(lbm_h h);

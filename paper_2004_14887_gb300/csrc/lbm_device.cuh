@@ -20,7 +20,7 @@
 
 namespace lbmg {
 
-enum : int { ST_NEWTON = 1, ST_NAN = 2 };
+enum : int { ST_NEWTON = 1, ST_NAN = 2, ST_TIMEOUT = 4 };
 enum : signed char { RK_FINE = 0, RK_TF = 1, RK_RING = 2 };
 enum : unsigned char { TILE_FAST = 0, TILE_SKIP = 1, TILE_GENERAL = 2 };
 enum : int { TAG_BULK = -1, TAG_HOLE = -2 };
@@ -113,6 +113,9 @@ struct LevelDev {
     int fast_lo[3], fast_hi[3];  // tile grown by 2 must stay in [fast_lo, fast_hi]
     int has_child;
     int child_lo[3], child_hi[3], child_per[3];  // closed child box in this level's box coordinates
+    // collision parameters of the level in both arithmetic types (batched launches read them here)
+    double om, sigma, spsi;
+    float tauf, omf, sigmaf, spsif;
     // hanging nodes of this level: table rows [ie_base, ie_base + n_ie), TF stencils
     int ie_base, n_ie;
     const int *ie_nst;

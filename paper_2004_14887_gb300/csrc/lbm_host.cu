@@ -87,6 +87,13 @@ struct lbm_hierarchy {
     double timing_ms[LBM_MAX_LEVELS] = {0, 0, 0, 0};
     int64_t timing_launches[LBM_MAX_LEVELS] = {0, 0, 0, 0};
     std::string err;
+    // batched hierarchies (lbm_create_batch): the batch owns its members
+    std::vector<lbm_hierarchy *> members;
+    lbm_hierarchy *batch = nullptr;  // set on members
+    BatchDev bdev{};
+    BatchPhase *d_phases = nullptr;
+    int nphases = 0;
+    int batch_grid = 0;
 };
 
 namespace {
@@ -717,6 +724,13 @@ LevelDev level_dev(const lbm_h h, int l)
     d.if_C = v.if_C;
     d.nif = std::max(1, v.nif);
     d.tau = v.tau;
+    d.om = 1.0 - 1.0 / v.tau;
+    d.sigma = h->d.sigma;
+    d.spsi = (double)h->d.psi_sign;
+    d.tauf = (float)d.tau;
+    d.omf = (float)d.om;
+    d.sigmaf = (float)d.sigma;
+    d.spsif = (float)d.spsi;
     tile_bounds(h, l, d.fast_lo, d.fast_hi, d.child_lo, d.child_hi, d.child_per);
     d.has_child = v.has_child ? 1 : 0;
     d.ie_base = v.nTFP;
@@ -1033,10 +1047,14 @@ int lbm_init_fields(lbm_h h, int level, const double *rho, const double *u, int 
     return LBM_OK;
 }
 
+static int batch_advance(lbm_h h, int64_t n);
+
 int lbm_advance(lbm_h h, int64_t n)
 {
     if (!h) return LBM_ERR_ARG;
     if (n < 0) return fail(h, LBM_ERR_ARG, "negative step count");
+    if (h->batch) return fail(h, LBM_ERR_ARG, "this hierarchy belongs to a batch: advance the batch");
+    if (!h->members.empty()) return batch_advance(h, n);
     for (int64_t s = 0; s < n; s++) {
         const long long k = h->ncoarse;
         int rc;
@@ -1105,6 +1123,7 @@ int lbm_check_status(lbm_h h)
     int st = 0;
     CK(cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     CK(cudaMemset(h->d_status, 0, sizeof(int)));
+    if (st & ST_TIMEOUT) return fail(h, LBM_ERR_TIMEOUT, "a grid barrier wait gave up");
     if (st & ST_NEWTON) return fail(h, LBM_ERR_NEWTON, "Newton did not converge at a TF node");
     if (st & ST_NAN) return fail(h, LBM_ERR_DIVERGED, "NaN or Inf met");
     return LBM_OK;
@@ -1165,7 +1184,14 @@ const char *lbm_last_error(lbm_h h) { return h ? h->err.c_str() : g_create_error
 void lbm_destroy(lbm_h h)
 {
     if (!h) return;
+    if (h->batch) return;  // members are destroyed with their batch
     if (h->stream) cudaStreamSynchronize(h->stream);
+    for (auto *m : h->members) {
+        m->batch = nullptr;
+        m->own_stream = false;
+        lbm_destroy(m);
+    }
+    h->members.clear();
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     for (auto &b : h->bufs) {
@@ -1251,3 +1277,204 @@ extern "C" int lbm_reduce_static(lbm_h h, int level, double out[4])
     if (st & ST_NAN) return fail(h, LBM_ERR_DIVERGED, "NaN or Inf in level %d", level);
     return LBM_OK;
 }
+
+
+// ================================================================== batches
+namespace {
+constexpr int kBatchThreads = T2X * T2YT;                        // 256
+constexpr int kBatchSeg = kBatchThreads / 16;                    // D2Q9 segments per block
+
+void emit_phases(std::vector<BatchPhase> &v, int l, int sub, int L)
+{
+    if (L > 1 || l > 0) v.push_back({PH_RH, l, sub, 0});
+    if (l + 1 < L) {
+        emit_phases(v, l + 1, 2 * sub, L);
+        emit_phases(v, l + 1, 2 * sub + 1, L);
+        v.back().join_next = 1;  // the child's last bulk pass is independent of what follows
+    }
+    if (l > 0) v.push_back({PH_GI, l, sub, 0});
+    v.push_back({PH_BULK, l, sub, 0});
+}
+
+int build_batch(lbm_h b)
+{
+    const int n = (int)b->members.size(), L = b->nl;
+    std::vector<LevelDev> lev((size_t)n * L);
+    std::vector<IfaceDev> ifc((size_t)n * L);
+    std::vector<int> pre_bulk((size_t)L * (n + 1), 0), pre_rh((size_t)L * (n + 1), 0), pre_gi((size_t)L * (n + 1), 0);
+    std::vector<int> nb_recon((size_t)L * n, 0), nb_grad((size_t)L * n, 0);
+    for (int hh = 0; hh < n; hh++) {
+        lbm_h m = b->members[hh];
+        for (int l = 0; l < L; l++) {
+            lev[(size_t)hh * L + l] = level_dev(m, l);
+            if (l > 0) ifc[(size_t)hh * L + l] = m->ifc[l].dev;
+            const Level &v = m->lev[l];
+            const int tiles = v.tiles[0] * v.tiles[1];
+            const int nr = l > 0 ? (m->ifc[l].dev.nTF + kBatchSeg - 1) / kBatchSeg : 0;
+            const int nh = l + 1 < L ? (m->ifc[l + 1].dev.nTF + m->ifc[l + 1].dev.nRing + kBatchSeg - 1) / kBatchSeg : 0;
+            const int ng = l > 0 ? (m->ifc[l].dev.nTF + kBatchSeg - 1) / kBatchSeg : 0;
+            const int ni = l > 0 ? (m->ifc[l].dev.nIE + kBatchSeg - 1) / kBatchSeg : 0;
+            nb_recon[(size_t)l * n + hh] = nr;
+            nb_grad[(size_t)l * n + hh] = ng;
+            const size_t o = (size_t)l * (n + 1);
+            pre_bulk[o + hh + 1] = pre_bulk[o + hh] + tiles;
+            pre_rh[o + hh + 1] = pre_rh[o + hh] + nr + nh;
+            pre_gi[o + hh + 1] = pre_gi[o + hh] + ng + ni;
+        }
+    }
+    lbm_h h = b;
+    bool ok = true;
+    BatchDev &B = b->bdev;
+    B.n = n;
+    B.L = L;
+    B.lev = upload(b, lev, &ok);
+    B.ifc = upload(b, ifc, &ok);
+    B.pre_bulk = upload(b, pre_bulk, &ok);
+    B.pre_rh = upload(b, pre_rh, &ok);
+    B.nb_recon = upload(b, nb_recon, &ok);
+    B.pre_gi = upload(b, pre_gi, &ok);
+    B.nb_grad = upload(b, nb_grad, &ok);
+    std::vector<BatchPhase> ph;
+    emit_phases(ph, 0, 0, L);
+    b->d_phases = upload(b, ph, &ok);
+    b->nphases = (int)ph.size();
+    unsigned int *bar = (unsigned int *)dev_alloc(b, 4 * sizeof(unsigned int));
+    b->d_status = (int *)dev_alloc(b, 2 * sizeof(int));
+    if (!ok || !bar || !b->d_status) return fail(b, LBM_ERR_OOM, "batch tables");
+    CK(cudaMemset(bar, 0, 4 * sizeof(unsigned int)));
+    CK(cudaMemset(b->d_status, 0, 2 * sizeof(int)));
+    b->d_maxit = b->d_status + 1;
+    B.bar_count = bar;
+    B.bar_gen = bar + 1;
+    B.status = b->d_status;
+    B.max_iters = b->d_maxit;
+    B.barrier_ns = 2000000000ull;  // 2 s
+    return LBM_OK;
+}
+
+template <typename S>
+int batch_launch(lbm_h b, long long k0, int nsteps)
+{
+    lbm_h h = b;
+    auto kern = k_batch<9, S, T2X, T2YT, T2NR>;
+    if (b->batch_grid == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, 0));
+        if (per_sm < 1) return fail(b, LBM_ERR_CUDA, "the batch kernel does not fit on an SM");
+        b->batch_grid = sms * per_sm;
+    }
+    BatchDev B = b->bdev;
+    const BatchPhase *ph = b->d_phases;
+    int np = b->nphases;
+    void *args[] = {&B, &ph, &np, &k0, &nsteps};
+    CK(cudaLaunchCooperativeKernel((void *)kern, dim3(b->batch_grid), dim3(kBatchThreads), args, 0, b->stream));
+    return LBM_OK;
+}
+}  // namespace
+
+static int batch_advance(lbm_h b, int64_t n)
+{
+    lbm_h h = b;
+    // every member counts the coarse steps done since its own initialisation
+    long long k = b->members[0]->ncoarse;
+    for (auto *m : b->members)
+        if (m->ncoarse != k) return fail(b, LBM_ERR_ARG, "batch members were initialised at different steps");
+    for (int64_t done = 0; done < n;) {
+        const int chunk = (int)std::min<int64_t>(n - done, 1 << 20);
+        int rc;
+        if (b->d.storage == LBM_F64) rc = batch_launch<double>(b, k + done, chunk);
+        else if (b->d.storage == LBM_F32) rc = batch_launch<float>(b, k + done, chunk);
+        else rc = batch_launch<__half>(b, k + done, chunk);
+        if (rc != LBM_OK) return rc;
+        b->launches++;
+        done += chunk;
+    }
+    for (auto *m : b->members) m->ncoarse += n;
+    b->ncoarse = k + n;
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+extern "C" {
+
+int lbm_create_batch(const lbm_hierarchy_desc *descs, int n, void *cuda_stream, lbm_h *out)
+{
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!descs || n < 1) return fail(nullptr, LBM_ERR_ARG, "need at least one description");
+    for (int i = 0; i < n; i++) {
+        if (descs[i].lattice != 9) return fail(nullptr, LBM_ERR_BAD_DESC, "batches hold D2Q9 hierarchies");
+        if (descs[i].storage != descs[0].storage || descs[i].n_levels != descs[0].n_levels)
+            return fail(nullptr, LBM_ERR_BAD_DESC, "batch members need the same storage and level count");
+    }
+    lbm_h b = new lbm_hierarchy();
+    b->d = descs[0];
+    b->Q = 9;
+    b->D = 2;
+    b->nl = descs[0].n_levels;
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return fail(nullptr, LBM_ERR_CUDA, "cudaStreamCreateWithFlags failed");
+        }
+        b->own_stream = true;
+    }
+    for (int i = 0; i < n; i++) {
+        lbm_h m = nullptr;
+        const int rc = lbm_create_hierarchy(&descs[i], (void *)b->stream, &m);
+        if (rc != LBM_OK) {
+            const std::string e = std::string("member ") + std::to_string(i) + ": " + lbm_create_error();
+            lbm_destroy(b);
+            return fail(nullptr, rc, "%s", e.c_str());
+        }
+        m->batch = b;
+        b->members.push_back(m);
+    }
+    const int rc = build_batch(b);
+    if (rc != LBM_OK) {
+        g_create_error = b->err;
+        lbm_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_member(lbm_h b, int i, lbm_h *member)
+{
+    if (!b || !member) return LBM_ERR_ARG;
+    if (i < 0 || i >= (int)b->members.size())
+        return fail(b, LBM_ERR_ARG, "member %d out of range [0,%d)", i, (int)b->members.size());
+    *member = b->members[i];
+    return LBM_OK;
+}
+
+int lbm_batch_check_barrier(lbm_h b, int skip_block, int64_t limit_us)
+{
+    lbm_h h = b;
+    if (!b || b->members.empty()) return b ? fail(b, LBM_ERR_ARG, "not a batch") : LBM_ERR_ARG;
+    if (limit_us < 1 || limit_us > 10000000) return fail(b, LBM_ERR_ARG, "limit must be in [1 us, 10 s]");
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaMemsetAsync(b->bdev.bar_count, 0, 2 * sizeof(unsigned int), b->stream));
+    CK(cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream));
+    unsigned int *cnt = b->bdev.bar_count, *gen = b->bdev.bar_gen;
+    int *st = b->d_status;
+    unsigned long long lim = (unsigned long long)limit_us * 1000ull;
+    void *args[] = {&cnt, &gen, &st, &lim, &skip_block};
+    CK(cudaLaunchCooperativeKernel((void *)k_barrier_check, dim3(sms), dim3(32), args, 0, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    int status = 0;
+    CK(cudaMemcpy(&status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(b->d_status, 0, sizeof(int)));
+    CK(cudaMemset(b->bdev.bar_count, 0, 2 * sizeof(unsigned int)));
+    if (status & ST_TIMEOUT) return fail(b, LBM_ERR_TIMEOUT, "a grid barrier wait gave up after %lld us", (long long)limit_us);
+    return LBM_OK;
+}
+
+}  // extern "C"

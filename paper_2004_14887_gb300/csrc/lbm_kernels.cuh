@@ -595,9 +595,9 @@ __device__ __forceinline__ void collide_store(const LevelDev &Lv, typename St<S>
 // 2(TX+TY)+4 halo nodes are shared out one per thread; all loads of a thread (its
 // nodes and its halo node) go out before any is used.
 template <int Q, typename S, int TX, int TYT, int NR>
-__global__ void __launch_bounds__(TX *TYT) k_bulk2d(LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
-                                                     typename St<S>::R tau, typename St<S>::R om,
-                                                     typename St<S>::R sigma, typename St<S>::R spsi)
+__device__ __forceinline__ void bulk2d_tile(const LevelDev &Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
+                                            typename St<S>::R tau, typename St<S>::R om, typename St<S>::R sigma,
+                                            typename St<S>::R spsi, int bx, int by)
 {
     using L = Lat<Q>;
     using R = typename St<S>::R;
@@ -611,9 +611,8 @@ __global__ void __launch_bounds__(TX *TYT) k_bulk2d(LevelDev Lv, const S *__rest
     static_assert(NB <= NT, "one halo node per thread at most");
     __shared__ R s_rho[H];
     __shared__ R s_u[D * H];
-
     const LevelGeo &g = Lv.g;
-    const int X0 = blockIdx.x * TX, Y0 = blockIdx.y * TY;
+    const int X0 = bx * TX, Y0 = by * TY;
     const int t0[3] = {X0, Y0, 0}, T[3] = {TX, TY, 1};
     const unsigned char flag = tile_class<D>(Lv, t0, T);
     if (flag == TILE_SKIP) return;
@@ -745,6 +744,14 @@ __global__ void __launch_bounds__(TX *TYT) k_bulk2d(LevelDev Lv, const S *__rest
         collide_store<Q, S, HX, HY, H>(Lv, f[r], rho[r], u[r], tag[r], hs, s_rho, s_u, tau, om, sigma, spsi, fdst,
                                        idx[r]);
     }
+}
+
+template <int Q, typename S, int TX, int TYT, int NR>
+__global__ void __launch_bounds__(TX *TYT, sizeof(S) == 8 ? 1 : 4) k_bulk2d(LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
+                                                     typename St<S>::R tau, typename St<S>::R om,
+                                                     typename St<S>::R sigma, typename St<S>::R spsi)
+{
+    bulk2d_tile<Q, S, TX, TYT, NR>(Lv, fsrc, fdst, tau, om, sigma, spsi, blockIdx.x, blockIdx.y);
 }
 
 // Geometric class of one plane p of a z-marching tile: LOAD_FAST when the tile grown by
@@ -974,6 +981,179 @@ __global__ void __launch_bounds__(TX *TY) k_bulk3d(LevelDev Lv, const S *__restr
         tc = tn;
         __syncthreads();
     }
+}
+
+
+// ------------------------------------------------------------------ batched persistent launch
+// Many independent hierarchies with the same number of levels advance together: the
+// sub-cycle schedule of one coarse step is a list of phases (history + Newton,
+// gradients + hanging nodes, bulk) and every phase is one grid-stride pass over the
+// work items of all hierarchies.  One cooperative launch runs all phases of n coarse
+// steps with a grid barrier between dependent phases.
+enum : int { PH_RH = 0, PH_GI = 1, PH_BULK = 2 };
+
+struct BatchPhase {
+    int kind, level, sub;  // level step index k_l = k * 2^level + sub for coarse step k
+    int join_next;         // the next phase is independent of this one: no barrier between
+};
+
+struct BatchDev {
+    int n, L;
+    const LevelDev *lev;    // [n][L]
+    const IfaceDev *ifc;    // [n][L]; ifc[h*L + l] couples levels l-1 and l
+    const int *pre_bulk;    // [L][n+1] prefix sums of bulk tiles
+    const int *pre_rh;      // [L][n+1] prefix sums of (Newton + history) blocks
+    const int *nb_recon;    // [L][n] Newton blocks of each hierarchy (the rest is history)
+    const int *pre_gi;      // [L][n+1] prefix sums of (gradient + hanging) blocks
+    const int *nb_grad;     // [L][n]
+    int *status, *max_iters;
+    unsigned int *bar_count, *bar_gen;
+    unsigned long long barrier_ns;  // a barrier wait longer than this gives up
+};
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of a cooperative launch.  Thread 0 of each block arrives on a
+// counter; the last arrival resets it and bumps the generation; the others wait for
+// the generation to change, at most limit_ns, after which they set ST_TIMEOUT and the
+// barrier returns false (the caller stops).
+__device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int *gen, unsigned int nblocks,
+                                             int *status, unsigned long long limit_ns)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned int *vgen = gen;
+        const unsigned int g0 = *vgen;
+        __threadfence();
+        if (atomicAdd(count, 1u) == nblocks - 1) {
+            *((volatile unsigned int *)count) = 0u;
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const unsigned long long t0 = globaltimer_ns();
+            while (*vgen == g0) {
+                if (globaltimer_ns() - t0 > limit_ns) {
+                    atomicOr(status, ST_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// hierarchy owning work item t: the last h with pre[h] <= t
+__device__ __forceinline__ int owner(const int *pre, int n, int t)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ TimeW batch_weights(int phase, long long kp)
+{
+    TimeW tw;
+    tw.slot[0] = (int)((kp + 2) % 3);
+    tw.slot[1] = (int)(kp % 3);
+    tw.slot[2] = (int)((kp + 1) % 3);
+    if (phase == 1) {
+        tw.w[0] = 0.0;
+        tw.w[1] = 0.0;
+        tw.w[2] = 1.0;
+    } else if (kp == 0) {
+        tw.w[0] = 0.0;
+        tw.w[1] = 0.5;
+        tw.w[2] = 0.5;
+    } else {
+        tw.w[0] = -1.0 / 8.0;  // Eq. (TempInt)
+        tw.w[1] = 3.0 / 4.0;
+        tw.w[2] = 3.0 / 8.0;
+    }
+    return tw;
+}
+
+template <int Q, typename S, int TX, int TYT, int NR>
+__global__ void __launch_bounds__(TX *TYT) k_batch(BatchDev B, const BatchPhase *__restrict__ phases, int nphases,
+                                                    long long k0, int nsteps)
+{
+    using R = typename St<S>::R;
+    const unsigned int nb = gridDim.x;
+    for (int st = 0; st < nsteps; st++) {
+        const long long k = k0 + st;
+        for (int pi = 0; pi < nphases; pi++) {
+            const BatchPhase ph = phases[pi];
+            const int l = ph.level;
+            const long long kl = (k << l) + ph.sub;
+            if (ph.kind == PH_BULK) {
+                const int *pre = B.pre_bulk + (size_t)l * (B.n + 1);
+                for (int t = blockIdx.x; t < pre[B.n]; t += nb) {
+                    const int h = owner(pre, B.n, t);
+                    const LevelDev &Lv = B.lev[h * B.L + l];
+                    const int local = t - pre[h];
+                    const bool dbl = sizeof(R) == 8;
+                    bulk2d_tile<Q, S, TX, TYT, NR>(Lv, (const S *)Lv.f[kl & 1], (S *)Lv.f[(kl + 1) & 1],
+                                                   dbl ? (R)Lv.tau : (R)Lv.tauf, dbl ? (R)Lv.om : (R)Lv.omf,
+                                                   dbl ? (R)Lv.sigma : (R)Lv.sigmaf, dbl ? (R)Lv.spsi : (R)Lv.spsif,
+                                                   local % Lv.tiles[0], local / Lv.tiles[0]);
+                    __syncthreads();  // the tile's shared arrays are reused by the next item
+                }
+            } else if (ph.kind == PH_RH) {
+                const int *pre = B.pre_rh + (size_t)l * (B.n + 1);
+                const TimeW tw = l > 0 ? batch_weights((int)(kl & 1), kl >> 1) : TimeW{};
+                for (int t = blockIdx.x; t < pre[B.n]; t += nb) {
+                    const int h = owner(pre, B.n, t);
+                    const int local = t - pre[h];
+                    const int nbr = B.nb_recon[(size_t)l * B.n + h];
+                    const LevelDev &F = B.lev[h * B.L + l];
+                    const S *fA = (const S *)F.f[kl & 1];
+                    if (local < nbr)
+                        recon_body<Q, S>(local, B.ifc[h * B.L + l], F, B.lev[h * B.L + l - 1], fA, tw, (int)(kl & 1),
+                                         B.status, B.max_iters);
+                    else
+                        hist_body<Q, S>(local - nbr, B.ifc[h * B.L + l + 1], F.g, fA, (int)((kl + 1) % 3), 0);
+                }
+            } else {
+                const int *pre = B.pre_gi + (size_t)l * (B.n + 1);
+                const TimeW tw = batch_weights((int)(kl & 1), kl >> 1);
+                for (int t = blockIdx.x; t < pre[B.n]; t += nb) {
+                    const int h = owner(pre, B.n, t);
+                    const int local = t - pre[h];
+                    const int nbg = B.nb_grad[(size_t)l * B.n + h];
+                    const LevelDev &F = B.lev[h * B.L + l];
+                    const S *fA = (const S *)F.f[kl & 1];
+                    if (local < nbg)
+                        grad_body<Q, S>(local, B.ifc[h * B.L + l], F, B.lev[h * B.L + l - 1], fA, tw, (int)(kl & 1));
+                    else
+                        ie_body<Q, S>(local - nbg, B.ifc[h * B.L + l], F, fA);
+                }
+            }
+            if (!ph.join_next && !grid_barrier(B.bar_count, B.bar_gen, nb, B.status, B.barrier_ns)) return;
+        }
+    }
+}
+
+// The barrier alone, for the bounded-wait check: with skip >= 0 that block returns
+// without arriving, so every other block's wait runs out and sets ST_TIMEOUT.
+__global__ void k_barrier_check(unsigned int *count, unsigned int *gen, int *status, unsigned long long limit_ns,
+                                int skip)
+{
+    if ((int)blockIdx.x == skip) return;
+    grid_barrier(count, gen, gridDim.x, status, limit_ns);
 }
 
 // ------------------------------------------------------------------ utilities

@@ -56,7 +56,8 @@ EXPORTS = [
     "lbm_create_hierarchy", "lbm_create_error", "lbm_query_level", "lbm_node_class", "lbm_init_fields",
     "lbm_advance", "lbm_get_macros", "lbm_get_pops", "lbm_reduce", "lbm_check_status", "lbm_max_newton_iters",
     "lbm_timing_enable", "lbm_timing_read", "lbm_launch_count", "lbm_device_bytes", "lbm_synchronize",
-    "lbm_last_error", "lbm_destroy", "lbm_reduce_static",
+    "lbm_last_error", "lbm_destroy", "lbm_reduce_static", "lbm_create_batch", "lbm_batch_member",
+    "lbm_batch_check_barrier",
 ]
 
 _lib = None
@@ -95,6 +96,9 @@ def lib():
     L.lbm_last_error.restype = C.c_char_p
     L.lbm_destroy.argtypes = [vp]
     L.lbm_destroy.restype = None
+    L.lbm_create_batch.argtypes = [C.POINTER(lbm_hierarchy_desc), C.c_int, vp, C.POINTER(vp)]
+    L.lbm_batch_member.argtypes = [vp, C.c_int, C.POINTER(vp)]
+    L.lbm_batch_check_barrier.argtypes = [vp, C.c_int, C.c_int64]
     _lib = L
     return L
 
@@ -290,3 +294,102 @@ class Hierarchy:
 
     def synchronize(self):
         self._check(lib().lbm_synchronize(self._h))
+
+
+class _Member(Hierarchy):
+    """A hierarchy owned by a Batch (no advance of its own)."""
+
+    def __init__(self, batch, handle):  # noqa: D401 - wraps an existing handle
+        self.torch = batch.torch
+        self.device = batch.device
+        self.stream = batch.stream
+        self._stream_obj = batch.stream
+        self._batch = batch
+        self._h = handle
+        self._alloc = None
+        info = self.query_level(0)
+        self.levels = [info]
+        n = 1
+        while True:
+            try:
+                self.levels.append(self.query_level(n))
+                n += 1
+            except LbmError:
+                break
+        self.n_levels = n
+        self.q = 9
+        self.D = 2
+
+    def close(self):
+        self._h = None  # the batch destroys its members
+
+
+class Batch:
+    """Many independent D2Q9 hierarchies advanced together by one persistent
+    cooperative launch per advance() (lbm_create_batch)."""
+
+    def __init__(self, descs, torch_alloc: bool = True, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required: the library has no CPU path")
+        L = lib()
+        self.torch = torch
+        self.device = torch.cuda.current_device()
+        cur = stream if stream is not None else torch.cuda.current_stream()
+        if cur.cuda_stream == 0:
+            cur = torch.cuda.Stream()
+        self.stream = cur
+        arr = (lbm_hierarchy_desc * len(descs))()
+        self._alloc = _TorchAllocator(torch, self.device, cur.cuda_stream) if torch_alloc else None
+        for i, d in enumerate(descs):
+            arr[i] = make_desc(d, use_graphs=False)
+            if self._alloc:
+                arr[i].alloc, arr[i].free = self._alloc.alloc, self._alloc.free
+        self._descs = arr
+        h = C.c_void_p()
+        rc = L.lbm_create_batch(arr, len(descs), C.c_void_p(cur.cuda_stream), C.byref(h))
+        if rc != LBM_OK:
+            raise LbmError(rc, L.lbm_create_error().decode())
+        self._h = h
+        self.members = []
+        for i in range(len(descs)):
+            m = C.c_void_p()
+            self._check(L.lbm_batch_member(h, i, C.byref(m)))
+            self.members.append(_Member(self, m))
+
+    def _check(self, rc):
+        if rc != LBM_OK:
+            raise LbmError(rc, lib().lbm_last_error(self._h).decode())
+
+    def advance(self, n):
+        self._check(lib().lbm_advance(self._h, int(n)))
+
+    def check_status(self):
+        self._check(lib().lbm_check_status(self._h))
+
+    def check_barrier(self, skip_block, limit_us):
+        return lib().lbm_batch_check_barrier(self._h, int(skip_block), int(limit_us))
+
+    def launch_count(self):
+        return lib().lbm_launch_count(self._h)
+
+    def device_bytes(self):
+        return lib().lbm_device_bytes(self._h) + sum(m.device_bytes() for m in self.members)
+
+    def synchronize(self):
+        self._check(lib().lbm_synchronize(self._h))
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            for m in self.members:
+                m._h = None
+            lib().lbm_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

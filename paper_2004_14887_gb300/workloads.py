@@ -275,6 +275,33 @@ def init_fields(desc: dict, l: int):
     return np.ascontiguousarray(rho.reshape(-1)), np.ascontiguousarray(u)
 
 
+def batch2d(n=96, steps=1000, seed=0, storage="f32", nu0=1e-5, sides=(96, 128, 192, 256, 384, 512, 768, 1024)):
+    """Independent 2-level D2Q9 hierarchies of seeded uneven sizes: coarse side drawn
+    uniformly from `sides`, a centred patch of half the side; each carries a seeded
+    barotropic vortex (swirl Mach U[0.02, 0.08], mean Mach U[0.05, 0.15], random
+    direction) or an acoustic pulse (amplitude log-uniform in [1e-4, 1e-3])."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        side = int(rng.choice(sides))
+        lo, hi = side // 4, 3 * side // 4
+        d = _base(9, (side, side), [((lo, lo), (hi, hi))], nu0, storage)
+        ang = rng.uniform(0.0, 2.0 * math.pi)
+        if rng.random() < 0.5:
+            mach = rng.uniform(0.05, 0.15) * CS
+            d["init"] = {"kind": "vortex", "xc": 0.5 * side + rng.uniform(-2, 2), "yc": 0.5 * side + rng.uniform(-2, 2),
+                         "Rc": side / 16.0, "swirl": float(rng.uniform(0.02, 0.08)),
+                         "U": (mach * math.cos(ang), mach * math.sin(ang), 0.0)}
+        else:
+            d["init"] = {"kind": "pulse", "xc": 0.5 * side + rng.uniform(-2, 2), "yc": 0.5 * side + rng.uniform(-2, 2),
+                         "zc": 0.0, "Rc": side / 64.0, "A": float(10.0 ** rng.uniform(-4.0, -3.0)),
+                         "U": (0.1 * CS * math.cos(ang), 0.1 * CS * math.sin(ang), 0.0)}
+        d["steps"] = steps
+        d["name"] = f"batch2d_{k}_{side}"
+        out.append(d)
+    return out
+
+
 CONFIGS = {
     "vortex2d_2lvl": lambda **kw: vortex2d(**kw),
     "pulse2d_3lvl": lambda **kw: pulse2d(**kw),

@@ -103,3 +103,18 @@ def test_host_geometry_and_tile_rule_accept_valid_hierarchies(L, desc):
         L.lbm_destroy(h)
     else:
         assert rc == lbm.LBM_ERR_CUDA, L.lbm_create_error().decode()
+
+
+def test_batch_validation_on_the_host(L):
+    """Batches take D2Q9 members with one storage and level count."""
+    from paper_2004_14887_gb300 import workloads as W
+
+    descs = W.batch2d(n=3, sides=(48, 64))
+    arr = (lbm.lbm_hierarchy_desc * 3)(*[lbm.make_desc(d) for d in descs])
+    arr[1].storage = 0 if arr[0].storage else 1
+    h = C.c_void_p()
+    assert L.lbm_create_batch(arr, 3, None, C.byref(h)) == lbm.LBM_ERR_BAD_DESC
+    arr[1].storage = arr[0].storage
+    arr[2].lattice = 19
+    assert L.lbm_create_batch(arr, 3, None, C.byref(h)) == lbm.LBM_ERR_BAD_DESC
+    assert L.lbm_create_batch(arr, 0, None, C.byref(h)) == lbm.LBM_ERR_ARG
