@@ -115,9 +115,11 @@ WORKLOAD_TEXT = {
                    "[128,384)^2 x [112,144), pulse 1e-4 + vortex at Mach 0.15",
     "vortex3d_3lvl_128": "vortex3d_3lvl_128: D3Q19, 3 levels, coarse 128^3 periodic, cubes 64^3 and 32^3 coarse "
                          "cells (half-size replica of vortex3d_3lvl, for profiling)",
+    "batch2d": "batch2d: 96 independent D2Q9 2-level hierarchies, coarse sides drawn from {96..1024}, centred "
+               "patches of half the side, seeded vortices or pulses, one persistent cooperative launch per step",
 }
 DEFAULT_STORAGE = {"pulse2d_3lvl": "f32", "vortex2d_2lvl": "f64", "vortex3d_3lvl": "f32", "slab3d_3lvl": "f16s",
-                   "vortex3d_3lvl_128": "f32"}
+                   "vortex3d_3lvl_128": "f32", "batch2d": "f32"}
 
 
 def _workloads():
@@ -125,7 +127,8 @@ def _workloads():
 
     return {"pulse2d_3lvl": W.pulse2d, "vortex2d_2lvl": W.vortex2d, "vortex3d_3lvl": W.vortex3d,
             "slab3d_3lvl": W.slab3d,
-            "vortex3d_3lvl_128": lambda **kw: W.vortex3d(n=128, boxes=((32, 96), (48, 80)), **kw)}
+            "vortex3d_3lvl_128": lambda **kw: W.vortex3d(n=128, boxes=((32, 96), (48, 80)), **kw),
+            "batch2d": W.batch2d}
 
 
 def _traffic_from_profiles(workload, storage):
@@ -150,6 +153,86 @@ def _traffic_from_profiles(workload, storage):
     except Exception:
         return None
     return None
+
+
+def run_batch(args):
+    """The batched workload: every step advances all hierarchies of the batch by one
+    coarse step in one cooperative persistent launch."""
+    import torch
+
+    from paper_2004_14887_gb300 import lbm
+    from paper_2004_14887_gb300 import workloads as W
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    torch.cuda.set_stream(torch.cuda.Stream())
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    storage = args.storage or DEFAULT_STORAGE["batch2d"]
+    descs = W.batch2d(storage=storage)
+    tc = time.perf_counter()
+    b = lbm.Batch(descs)
+    for d, m in zip(descs, b.members):
+        for l in range(m.n_levels):
+            r, u = W.init_fields(d, l)
+            m.init_fields(l, r, u)
+    print(f"[bench] batch2d {storage}: {len(descs)} hierarchies, set-up {time.perf_counter() - tc:.2f} s, "
+          f"{b.device_bytes() / 1e9:.2f} GB on the device", file=sys.stderr, flush=True)
+    upd = sum(W.updates_per_coarse_step(d) for d in descs)
+    feq = sum(W.fine_equivalent_per_coarse_step(d) for d in descs)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    K, Wm = args.steps, args.warmup
+    b.advance(Wm)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    n0 = b.launch_count()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as cs:
+        for k in range(K):
+            flush.zero_()
+            starts[k].record()
+            b.advance(1)
+            ends[k].record()
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    b.check_status()
+    ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
+    if ws > 1:
+        t_ = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t_, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t_.item())
+    t = ms / 1e3
+    peak, peak_src = _peaks()
+    bytes_step = upd * 2 * 9 * BYTES_PER_POP[storage]
+    line = {
+        "metric": METRIC, "value": ws * feq * K / t / 1e6, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
+        "ms_per_step": 1e3 * t / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": storage, "data": "synthetic (seeded analytic fields, no dataset)",
+        "config": {"workload": WORKLOAD_TEXT["batch2d"] + f", {storage} storage", "hierarchies": len(descs),
+                   "node_updates_per_step": upd, "fine_equivalent_updates_per_step": feq,
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+        "actual_mlups": ws * upd * K / t / 1e6,
+        "roofline": {"bound": "hbm", "achieved": bytes_step / (t / K) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": bytes_step / (t / K) / 1e9 / peak, "traffic": None,
+                     "kernel": "k_batch (the whole step is one persistent launch)",
+                     "algorithmic_bytes_per_launch": bytes_step, "avg_launch_ms": 1e3 * t / K,
+                     "peak_source": f"{peak_src} hbm_gbs"},
+        "gpu_launches": b.launch_count() - n0,
+        "clocks": cs.summary(),
+        "e2e": None,
+    }
+    b.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
 
 
 def run_gb300(args):
@@ -422,6 +505,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch2d":
+        run_batch(args)
     else:
         run_gb300(args)
 

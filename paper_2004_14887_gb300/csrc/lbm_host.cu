@@ -1368,6 +1368,8 @@ int batch_launch(lbm_h b, long long k0, int nsteps)
     BatchDev B = b->bdev;
     const BatchPhase *ph = b->d_phases;
     int np = b->nphases;
+    // a barrier that gave up in an earlier launch leaves its counter behind
+    CK(cudaMemsetAsync(B.bar_count, 0, sizeof(unsigned int), b->stream));
     void *args[] = {&B, &ph, &np, &k0, &nsteps};
     CK(cudaLaunchCooperativeKernel((void *)kern, dim3(b->batch_grid), dim3(kBatchThreads), args, 0, b->stream));
     return LBM_OK;
