@@ -161,6 +161,25 @@ LBM_API int lbm_reduce(lbm_h h, int level, double out[4]);
 #define LBM_STATIC_REDUCE_PARTIALS 4096
 LBM_API int lbm_reduce_static(lbm_h h, int level, double out[4]);
 
+/* Probes: density time series at n points xyz[3n] (level-0 node units; z ignored in
+ * 2-D), sampled after every coarse step of lbm_advance by (bi/tri)linear interpolation
+ * of the zeroth moment over the cell of the finest level that holds the point.  At
+ * most `capacity` rows are recorded (later steps are not sampled).  Setting probes
+ * resets the recorded rows.  LBM_ERR_ARG if a point lies on no level's active cells.
+ * lbm_get_probes writes the rows recorded so far to out[rows][n] (host; may be NULL
+ * to query *n_samples) and synchronises the stream. */
+LBM_API int lbm_set_probes(lbm_h h, int n, const double *xyz, int64_t capacity);
+LBM_API int lbm_get_probes(lbm_h h, double *out, int64_t *n_samples);
+
+/* Checkpoint: the state after a completed coarse step (every level's populations, the
+ * interface histories of Eq. (TempInt) and the step counter) as one host buffer.
+ * lbm_save_state with buf == NULL returns the size in *len; lbm_load_state restores
+ * a state saved from a hierarchy of the same description (checked: lattice, storage,
+ * levels, box sizes), after which lbm_advance continues bit for bit as the saved run
+ * would have.  Both synchronise the stream. */
+LBM_API int lbm_save_state(lbm_h h, void *buf, size_t *len);
+LBM_API int lbm_load_state(lbm_h h, const void *buf, size_t len);
+
 /* Batches of independent hierarchies (cfg. "many hierarchies of uneven sizes"):
  * lbm_create_batch builds n D2Q9 hierarchies with the same storage and level count
  * on one stream; lbm_advance on the batch advances all of them together in ONE

@@ -87,6 +87,11 @@ struct lbm_hierarchy {
     double timing_ms[LBM_MAX_LEVELS] = {0, 0, 0, 0};
     int64_t timing_launches[LBM_MAX_LEVELS] = {0, 0, 0, 0};
     std::string err;
+    // probes
+    ProbeDev probes{};
+    LevelDev *d_levs = nullptr;     // level views for the probe kernel
+    long long *d_kstep = nullptr;   // per-level step index of the current state
+    int64_t probe_rows = 0;
     // batched hierarchies (lbm_create_batch): the batch owns its members
     std::vector<lbm_hierarchy *> members;
     lbm_hierarchy *batch = nullptr;  // set on members
@@ -867,6 +872,11 @@ struct Sched {
                                                                              rho, u, pops);
     }
 
+    static void probe(lbm_h h, const long long *kstep, int row, int n)
+    {
+        k_probe<Q, S><<<(n + 63) / 64, 64, 0, h->stream>>>(h->probes, h->d_levs, kstep, row);
+    }
+
     static void reduce(lbm_h h, int l)
     {
         Level &v = h->lev[l];
@@ -1049,6 +1059,25 @@ int lbm_init_fields(lbm_h h, int level, const double *rho, const double *u, int 
 
 static int batch_advance(lbm_h h, int64_t n);
 
+// one row of probe samples for the current state (stream-ordered)
+static int record_probes(lbm_h h)
+{
+    std::vector<long long> ks(h->nl);
+    for (int l = 0; l < h->nl; l++) ks[l] = h->ncoarse << l;
+    CK(cudaMemcpyAsync(h->d_kstep + (size_t)(h->probe_rows % 64) * LBM_MAX_LEVELS, ks.data(), h->nl * sizeof(long long),
+                       cudaMemcpyHostToDevice, h->stream));
+    const int n = h->probes.n;
+    const int row = (int)h->probe_rows;
+    const long long *kp = h->d_kstep + (size_t)(h->probe_rows % 64) * LBM_MAX_LEVELS;
+    dispatch(h, [&](auto s) {
+        using Sc = decltype(s);
+        Sc::probe(h, kp, row, n);
+    });
+    h->probe_rows++;
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
 int lbm_advance(lbm_h h, int64_t n)
 {
     if (!h) return LBM_ERR_ARG;
@@ -1062,6 +1091,10 @@ int lbm_advance(lbm_h h, int64_t n)
         else rc = issue_coarse_step(h, k);
         if (rc != LBM_OK) return rc;
         h->ncoarse++;
+        if (h->probes.n > 0 && h->probe_rows < h->probes.capacity) {
+            rc = record_probes(h);
+            if (rc != LBM_OK) return rc;
+        }
     }
     return LBM_OK;
 }
@@ -1476,6 +1509,188 @@ int lbm_batch_check_barrier(lbm_h b, int skip_block, int64_t limit_us)
     CK(cudaMemset(b->d_status, 0, sizeof(int)));
     CK(cudaMemset(b->bdev.bar_count, 0, 2 * sizeof(unsigned int)));
     if (status & ST_TIMEOUT) return fail(b, LBM_ERR_TIMEOUT, "a grid barrier wait gave up after %lld us", (long long)limit_us);
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+
+// ================================================================== probes and state
+extern "C" {
+
+int lbm_set_probes(lbm_h h, int n, const double *xyz, int64_t capacity)
+{
+    if (!h || h->batch || !h->members.empty()) return h ? fail(h, LBM_ERR_ARG, "probes belong to single hierarchies") : LBM_ERR_ARG;
+    if (n < 0 || n > 65536 || (n > 0 && !xyz) || capacity < 0 || capacity > (1 << 26))
+        return fail(h, LBM_ERR_ARG, "bad probe count, positions or capacity");
+    if ((int64_t)n * capacity > ((int64_t)1 << 28)) return fail(h, LBM_ERR_ARG, "probe buffer above 2^28 samples");
+    std::vector<int> level(n), node((size_t)n * 8, 0);
+    std::vector<double> w((size_t)n * 8, 0.0);
+    const int nc = h->D == 3 ? 8 : 4;
+    for (int j = 0; j < n; j++) {
+        int found = -1;
+        for (int l = h->nl - 1; l >= 0 && found < 0; l--) {
+            const Level &v = h->lev[l];
+            const double sc = std::ldexp(1.0, l);
+            int64_t base[3];
+            double fr[3];
+            bool ok = true;
+            for (int a = 0; a < 3; a++) {
+                if (a >= h->D) {
+                    base[a] = 0;
+                    fr[a] = 0.0;
+                    continue;
+                }
+                const double q = xyz[3 * j + a] * sc - (double)v.off[a];
+                double fl = std::floor(q);
+                fr[a] = q - fl;
+                base[a] = (int64_t)fl;
+                if (v.per[a]) continue;
+                if (base[a] < 0 || base[a] + 1 > v.n[a] - 1) ok = false;
+            }
+            if (!ok) continue;
+            int idx[8];
+            double ww[8];
+            for (int c = 0; c < nc && ok; c++) {
+                int64_t p[3];
+                double wc = 1.0;
+                for (int a = 0; a < 3; a++) {
+                    const int bit = (c >> a) & 1;
+                    p[a] = base[a] + (a < h->D ? bit : 0) + v.off[a];
+                    if (a < h->D) wc *= bit ? fr[a] : 1.0 - fr[a];
+                }
+                const long long id = node_of(h, l, p);
+                if (id < 0) ok = false;
+                else {
+                    idx[c] = (int)id;
+                    ww[c] = wc;
+                }
+            }
+            if (!ok) continue;
+            found = l;
+            for (int c = 0; c < nc; c++) {
+                node[(size_t)j * 8 + c] = idx[c];
+                w[(size_t)j * 8 + c] = ww[c];
+            }
+        }
+        if (found < 0) return fail(h, LBM_ERR_ARG, "probe %d lies on no level's active cells", j);
+        level[j] = found;
+    }
+    bool ok = true;
+    ProbeDev P{};
+    P.n = n;
+    P.capacity = (int)capacity;
+    P.level = upload(h, level, &ok);
+    P.node = upload(h, node, &ok);
+    P.w = upload(h, w, &ok);
+    P.samples = (double *)dev_alloc(h, std::max<size_t>(1, (size_t)n * capacity) * sizeof(double));
+    if (!h->d_levs) {
+        std::vector<LevelDev> lv(h->nl);
+        for (int l = 0; l < h->nl; l++) lv[l] = level_dev(h, l);
+        h->d_levs = upload(h, lv, &ok);
+        h->d_kstep = (long long *)dev_alloc(h, 64 * LBM_MAX_LEVELS * sizeof(long long));
+    }
+    if (!ok || !P.samples || !h->d_kstep) return fail(h, LBM_ERR_OOM, "probe buffers");
+    h->probes = P;
+    h->probe_rows = 0;
+    return LBM_OK;
+}
+
+int lbm_get_probes(lbm_h h, double *out, int64_t *n_samples)
+{
+    if (!h || !n_samples) return h ? fail(h, LBM_ERR_ARG, "n_samples is NULL") : LBM_ERR_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    *n_samples = h->probe_rows;
+    if (out && h->probes.n > 0 && h->probe_rows > 0)
+        CK(cudaMemcpy(out, h->probes.samples, (size_t)h->probe_rows * h->probes.n * sizeof(double),
+                      cudaMemcpyDeviceToHost));
+    return LBM_OK;
+}
+
+// state = magic, version, lattice, storage, levels, coarse step, per-level box sizes,
+// then each level's current populations and each interface's history, raw.
+static const uint64_t kStateMagic = 0x4c424d4443535431ull;  // "LBMDCST1"
+
+static size_t state_bytes(const lbm_h h)
+{
+    size_t b = 8 * 8 + 8 * LBM_MAX_LEVELS;
+    const size_t ss = store_size(h->d.storage), as = arith_size(h->d.storage);
+    for (int l = 0; l < h->nl; l++) b += (size_t)h->Q * h->lev[l].pitch * ss;
+    for (int l = 1; l < h->nl; l++)
+        b += (size_t)3 * h->Q * std::max(1, h->ifc[l].dev.nTF) * as + (size_t)3 * 4 * std::max(1, h->ifc[l].dev.nRing) * as;
+    return b;
+}
+
+int lbm_save_state(lbm_h h, void *buf, size_t *len)
+{
+    if (!h || !len) return h ? fail(h, LBM_ERR_ARG, "len is NULL") : LBM_ERR_ARG;
+    if (!h->members.empty()) return fail(h, LBM_ERR_ARG, "save the members of a batch one by one");
+    const size_t need = state_bytes(h);
+    if (!buf) {
+        *len = need;
+        return LBM_OK;
+    }
+    if (*len < need) return fail(h, LBM_ERR_ARG, "buffer of %zu bytes, %zu needed", *len, need);
+    CK(cudaStreamSynchronize(h->stream));
+    uint64_t *hd = (uint64_t *)buf;
+    hd[0] = kStateMagic;
+    hd[1] = 1;
+    hd[2] = (uint64_t)h->Q;
+    hd[3] = (uint64_t)h->d.storage;
+    hd[4] = (uint64_t)h->nl;
+    hd[5] = (uint64_t)h->ncoarse;
+    hd[6] = 0;
+    hd[7] = 0;
+    for (int l = 0; l < LBM_MAX_LEVELS; l++) hd[8 + l] = l < h->nl ? (uint64_t)h->lev[l].N : 0;
+    char *p = (char *)buf + 8 * 8 + 8 * LBM_MAX_LEVELS;
+    const size_t ss = store_size(h->d.storage), as = arith_size(h->d.storage);
+    for (int l = 0; l < h->nl; l++) {
+        const Level &v = h->lev[l];
+        const size_t b = (size_t)h->Q * v.pitch * ss;
+        CK(cudaMemcpy(p, v.f[(h->ncoarse << l) & 1], b, cudaMemcpyDeviceToHost));
+        p += b;
+    }
+    for (int l = 1; l < h->nl; l++) {
+        const IfaceDev &I = h->ifc[l].dev;
+        const size_t bf = (size_t)3 * h->Q * std::max(1, I.nTF) * as, bm = (size_t)3 * 4 * std::max(1, I.nRing) * as;
+        CK(cudaMemcpy(p, I.hist_f, bf, cudaMemcpyDeviceToHost));
+        p += bf;
+        CK(cudaMemcpy(p, I.hist_m, bm, cudaMemcpyDeviceToHost));
+        p += bm;
+    }
+    *len = need;
+    return LBM_OK;
+}
+
+int lbm_load_state(lbm_h h, const void *buf, size_t len)
+{
+    if (!h || !buf) return h ? fail(h, LBM_ERR_ARG, "buf is NULL") : LBM_ERR_ARG;
+    if (!h->members.empty()) return fail(h, LBM_ERR_ARG, "load the members of a batch one by one");
+    const size_t need = state_bytes(h);
+    const uint64_t *hd = (const uint64_t *)buf;
+    if (len < need || hd[0] != kStateMagic || hd[1] != 1 || hd[2] != (uint64_t)h->Q ||
+        hd[3] != (uint64_t)h->d.storage || hd[4] != (uint64_t)h->nl)
+        return fail(h, LBM_ERR_ARG, "state does not belong to this hierarchy (lattice, storage, levels or size)");
+    for (int l = 0; l < h->nl; l++)
+        if (hd[8 + l] != (uint64_t)h->lev[l].N) return fail(h, LBM_ERR_ARG, "level %d has another box", l);
+    CK(cudaStreamSynchronize(h->stream));
+    h->ncoarse = (long long)hd[5];
+    const char *p = (const char *)buf + 8 * 8 + 8 * LBM_MAX_LEVELS;
+    const size_t ss = store_size(h->d.storage), as = arith_size(h->d.storage);
+    for (int l = 0; l < h->nl; l++) {
+        const Level &v = h->lev[l];
+        const size_t b = (size_t)h->Q * v.pitch * ss;
+        CK(cudaMemcpy(v.f[(h->ncoarse << l) & 1], p, b, cudaMemcpyHostToDevice));
+        p += b;
+    }
+    for (int l = 1; l < h->nl; l++) {
+        const IfaceDev &I = h->ifc[l].dev;
+        const size_t bf = (size_t)3 * h->Q * std::max(1, I.nTF) * as, bm = (size_t)3 * 4 * std::max(1, I.nRing) * as;
+        CK(cudaMemcpy(I.hist_f, p, bf, cudaMemcpyHostToDevice));
+        p += bf;
+        CK(cudaMemcpy(I.hist_m, p, bm, cudaMemcpyHostToDevice));
+        p += bm;
+    }
     return LBM_OK;
 }
 

@@ -1156,6 +1156,38 @@ __global__ void k_barrier_check(unsigned int *count, unsigned int *gen, int *sta
     grid_barrier(count, gen, gridDim.x, status, limit_ns);
 }
 
+
+// ------------------------------------------------------------------ probes
+// Density at probe points: (bi/tri)linear interpolation of rho over the 4 (8) nodes of
+// the finest level whose cell holds the point; rho of a node is the zeroth moment of
+// its current populations.  One thread per probe, one row of samples per call.
+struct ProbeDev {
+    int n;
+    const int *level;     // [n]
+    const int *node;      // [n][8] node indices in the level box
+    const double *w;      // [n][8] weights
+    double *samples;      // [capacity][n]
+    int capacity;
+};
+
+template <int Q, typename S>
+__global__ void k_probe(ProbeDev P, const LevelDev *__restrict__ levs, const long long *__restrict__ kstep, int row)
+{
+    using L = Lat<Q>;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P.n || row >= P.capacity) return;
+    const int l = P.level[j];
+    const LevelDev &Lv = levs[l];
+    const S *f = (const S *)Lv.f[kstep[l] & 1];
+    double acc = 0.0;
+    for (int c = 0; c < (L::D == 3 ? 8 : 4); c++) {
+        const int idx = P.node[j * 8 + c];
+        double r = 0.0;
+        for (int i = 0; i < Q; i++) r += (double)St<S>::ld(f + (long long)i * Lv.g.pitch, idx, L::w(i));
+        acc += P.w[j * 8 + c] * r;
+    }
+    P.samples[(long long)row * P.n + j] = acc;
+}
 // ------------------------------------------------------------------ utilities
 template <int Q, typename S>
 __global__ void k_init(LevelGeo g, const int *__restrict__ tag, const double *__restrict__ rho,

@@ -57,7 +57,7 @@ EXPORTS = [
     "lbm_advance", "lbm_get_macros", "lbm_get_pops", "lbm_reduce", "lbm_check_status", "lbm_max_newton_iters",
     "lbm_timing_enable", "lbm_timing_read", "lbm_launch_count", "lbm_device_bytes", "lbm_synchronize",
     "lbm_last_error", "lbm_destroy", "lbm_reduce_static", "lbm_create_batch", "lbm_batch_member",
-    "lbm_batch_check_barrier",
+    "lbm_batch_check_barrier", "lbm_set_probes", "lbm_get_probes", "lbm_save_state", "lbm_load_state",
 ]
 
 _lib = None
@@ -99,6 +99,10 @@ def lib():
     L.lbm_create_batch.argtypes = [C.POINTER(lbm_hierarchy_desc), C.c_int, vp, C.POINTER(vp)]
     L.lbm_batch_member.argtypes = [vp, C.c_int, C.POINTER(vp)]
     L.lbm_batch_check_barrier.argtypes = [vp, C.c_int, C.c_int64]
+    L.lbm_set_probes.argtypes = [vp, C.c_int, dp, C.c_int64]
+    L.lbm_get_probes.argtypes = [vp, dp, i64p]
+    L.lbm_save_state.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
+    L.lbm_load_state.argtypes = [vp, vp, C.c_size_t]
     _lib = L
     return L
 
@@ -273,6 +277,32 @@ class Hierarchy:
 
     def check_status(self):
         self._check(lib().lbm_check_status(self._h))
+
+    def set_probes(self, xyz, capacity):
+        """Density probes at points xyz [n, 3] (level-0 units), sampled after every coarse step."""
+        xyz = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
+        self._n_probes = xyz.shape[0]
+        self._check(lib().lbm_set_probes(self._h, xyz.shape[0], xyz.ctypes.data_as(C.POINTER(C.c_double)),
+                                         int(capacity)))
+
+    def get_probes(self):
+        n = C.c_int64()
+        self._check(lib().lbm_get_probes(self._h, None, C.byref(n)))
+        out = np.zeros((n.value, getattr(self, "_n_probes", 0)))
+        if out.size:
+            self._check(lib().lbm_get_probes(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(n)))
+        return out
+
+    def save_state(self):
+        n = C.c_size_t()
+        self._check(lib().lbm_save_state(self._h, None, C.byref(n)))
+        buf = np.zeros(n.value, dtype=np.uint8)
+        self._check(lib().lbm_save_state(self._h, buf.ctypes.data_as(C.c_void_p), C.byref(n)))
+        return buf
+
+    def load_state(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._check(lib().lbm_load_state(self._h, buf.ctypes.data_as(C.c_void_p), buf.size))
 
     def max_newton_iters(self):
         return lib().lbm_max_newton_iters(self._h)
