@@ -45,29 +45,50 @@ def test_load_rejects_foreign_state():
         b.load_state(a.save_state())
 
 
+def _oracle_probe(o, x, y):
+    """Bilinear density over the cell of the finest oracle level that holds (x, y)."""
+    for l in reversed(range(o.n_levels)):
+        lv = o.levels[l]
+        n, off, per = lv["n"], lv["off"], lv["periodic"]
+        qx, qy = x * 2 ** l - off[0], y * 2 ** l - off[1]
+        bx, by = int(math.floor(qx)), int(math.floor(qy))
+        cells = [(bx, by), (bx + 1, by), (bx, by + 1), (bx + 1, by + 1)]
+        cls = o.node_class(l).reshape(n[1], n[0])
+        ok = True
+        for cx, cy in cells:
+            if not per[0] and not 0 <= cx < n[0]:
+                ok = False
+            if not per[1] and not 0 <= cy < n[1]:
+                ok = False
+            if ok and cls[cy % n[1], cx % n[0]] == O.HOLE:
+                ok = False
+        if not ok:
+            continue
+        rho = o.macros(l)[0].reshape(n[1], n[0])
+        fx, fy = qx - bx, qy - by
+        ws = [(1 - fx) * (1 - fy), fx * (1 - fy), (1 - fx) * fy, fx * fy]
+        return sum(w * rho[cy % n[1], cx % n[0]] for w, (cx, cy) in zip(ws, cells))
+    raise AssertionError("no level holds the point")
+
+
 def test_probes_sample_interpolated_density():
     """A ring of 36 probes (Sec. 4.2 uses 36 pressure probes on a circle), sampled
-    every coarse step, equals the bilinear interpolation of the oracle's density."""
+    every coarse step, equals the bilinear interpolation of the oracle's density on
+    the finest level holding each point (the ring crosses levels 1 and 2)."""
     d = W.pulse2d(n=64, boxes=((16, 48), (24, 40)), Rc_finest=3.0)
     g = _make(d)
     o = O.Hierarchy(d)
     for l in range(o.n_levels):
         r, u = W.init_fields(d, l)
         o.init(l, r, u)
+    xc, yc = d["init"]["xc"], d["init"]["yc"]
     ang = np.arange(36) * 2 * math.pi / 36
-    pts = np.stack([32 + 24 * np.cos(ang), 32 + 24 * np.sin(ang), 0 * ang], 1)
+    pts = np.stack([xc + 9.3 * np.cos(ang), yc + 9.3 * np.sin(ang), 0 * ang], 1)
     g.set_probes(pts, capacity=10)
     g.advance(6)
     o.advance(6)
     got = g.get_probes()
     assert got.shape == (6, 36)
-    # level 0 holds every ring point (radius 24 > the level-1 patch half-width 16)
-    rho, _ = o.macros(0)
-    rho = rho.reshape(64, 64)
-    x, y = pts[:, 0], pts[:, 1]
-    x0, y0 = np.floor(x).astype(int), np.floor(y).astype(int)
-    fx, fy = x - x0, y - y0
-    want = (rho[y0, x0] * (1 - fx) * (1 - fy) + rho[y0, (x0 + 1) % 64] * fx * (1 - fy)
-            + rho[(y0 + 1) % 64, x0] * (1 - fx) * fy + rho[(y0 + 1) % 64, (x0 + 1) % 64] * fx * fy)
+    want = np.array([_oracle_probe(o, x, y) for x, y in pts[:, :2]])
     assert np.max(np.abs(got[-1] - want)) < 1e-12
     assert np.max(np.abs(got[-1] - 1.0)) > 1e-7  # the pulse has reached the ring
