@@ -98,6 +98,25 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x, device="cpu"):
+    """The largest x over the ranks of the default process group (x itself when there
+    is none): the job's time is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world_size, seconds):
+    """Units per second of the whole job: every rank processes units_per_rank
+    (independent replicas), the job lasts as long as its slowest rank."""
+    return world_size * units_per_rank / seconds
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -258,14 +277,8 @@ def run_gb300(args):
 
             dist.barrier()
 
-    def max_over_ranks(x):
-        if ws == 1:
-            return x
-        import torch.distributed as dist
-
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_over_ranks_gpu(x):
+        return max_over_ranks(x, device="cuda")
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
 
@@ -318,9 +331,9 @@ def run_gb300(args):
     upd = W.updates_per_coarse_step(d)
     feq = W.fine_equivalent_per_coarse_step(d)
     dev_ms, wall, launches, clocks = timed(h, K, Wm, sampler_dev=local)
-    t = max_over_ranks(dev_ms) / 1e3
-    value = ws * feq * K / t / 1e6
-    actual = ws * upd * K / t / 1e6
+    t = max_over_ranks_gpu(dev_ms) / 1e3
+    value = whole_job_rate(feq * K, ws, t) / 1e6
+    actual = whole_job_rate(upd * K, ws, t) / 1e6
 
     # dominant kernel: the bulk collide-and-stream of the finest level (4 launches per step)
     L = h.n_levels
@@ -344,7 +357,7 @@ def run_gb300(args):
             dv, hv = make(st)
             Kv = min(K, args.variant_steps if st == "f64" else K)
             dms, _, _, _ = timed(hv, Kv, max(3, Wm // 2))
-            tv = max_over_ranks(dms) / 1e3
+            tv = max_over_ranks_gpu(dms) / 1e3
             hv.timing_enable(True)
             for _ in range(min(Kv, 100)):
                 flush.zero_()
@@ -390,7 +403,7 @@ def run_gb300(args):
             he.get_macros(l, out=outs[l])
         torch.cuda.synchronize()
         barrier()
-        tw = max_over_ranks(time.perf_counter() - te)
+        tw = max_over_ranks_gpu(time.perf_counter() - te)
         h2d = sum(a.nbytes + b.nbytes for a, b in fields)
         d2h = sum(a.nbytes + b.nbytes for a, b in outs)
         e2e = {"value": ws * feq * K / tw / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
