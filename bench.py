@@ -288,6 +288,9 @@ def run_gb300(args):
         h = lbm.Hierarchy(d, use_graphs=use_graphs)
         print(f"[bench] {args.workload} {storage}: set-up {time.perf_counter() - tc:.2f} s, "
               f"{h.device_bytes() / 1e9:.2f} GB on the device", file=sys.stderr, flush=True)
+        if not args.no_autotune:
+            res = h.autotune(reps=10)
+            print(f"[bench] autotuned tile shapes per level: {res['cfg']}", file=sys.stderr, flush=True)
         for l in range(h.n_levels):
             r, u = W.init_fields(d, l)
             h.init_fields(l, r, u)
@@ -513,6 +516,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

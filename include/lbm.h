@@ -36,6 +36,7 @@ extern "C" {
 #endif
 
 #define LBM_MAX_LEVELS 4
+#define LBM_TILE_CONFIGS 5
 
 #if defined(__GNUC__)
 #define LBM_API __attribute__((visibility("default")))
@@ -206,6 +207,18 @@ LBM_API int lbm_batch_check_barrier(lbm_h batch, int skip_block, int64_t limit_u
 LBM_API int lbm_check_status(lbm_h h);
 /* Largest Newton iteration count met since creation. */
 LBM_API int lbm_max_newton_iters(lbm_h h);
+
+/* Autotuner for the D2Q9 bulk kernel.  LBM_TILE_CONFIGS tile shapes are compiled
+ * (threads x rows per thread): 0 = 32x8 threads x 2 rows, 1 = 32x4 x 4, 2 = 32x8 x 1,
+ * 3 = 64x4 x 2, 4 = 32x16 x 1.  lbm_autotune times reps launches of every shape on
+ * every level (on the current state, which it leaves unchanged) and keeps the fastest
+ * per level; us_out (optional, n_levels x LBM_TILE_CONFIGS) receives the measured
+ * microseconds per launch.  A D3Q19 hierarchy has one shape (no-op).  Synchronises.
+ * lbm_set_tile_config / lbm_get_tile_config set or read a level's shape directly (e.g.
+ * from a cache of earlier autotune results); changing a shape drops the captured graphs. */
+LBM_API int lbm_autotune(lbm_h h, int reps, double *us_out);
+LBM_API int lbm_set_tile_config(lbm_h h, int level, int cfg);
+LBM_API int lbm_get_tile_config(lbm_h h, int level, int *cfg);
 
 /* Kernel timing: while enabled, lbm_advance launches eagerly and brackets every
  * bulk collide-and-stream launch with CUDA events on the handle's stream.

@@ -90,6 +90,10 @@ template <> struct St<__half> {
     }
 };
 
+// correctly rounded reciprocal (IEEE round-to-nearest in both types)
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
 // ------------------------------------------------------------------ device views
 struct LevelGeo {
     int n[3];

@@ -39,6 +39,7 @@ struct Level {
     std::vector<unsigned char> tile_flag;
     int tiles[3] = {1, 1, 1};
     int nTFP = 0, nIE = 0, nTFC = 0, nif = 0;
+    int tile_cfg = 0;  // D2Q9 bulk tile shape (kTileCfgs), chosen by lbm_autotune
     int64_t n_active = 0;
     // child-box in this level's node coordinates, for volume weights
     bool has_child = false;
@@ -480,6 +481,12 @@ int build_interfaces(lbm_h h)
 
 constexpr int T2X = 32, T2YT = 8, T2NR = 2;  // D2Q9 tile: 32 x 8 threads, 2 rows per thread
 constexpr int T2Y = T2YT * T2NR;
+
+// D2Q9 bulk tile shapes the autotuner chooses from: threads (TX x TYT), NR rows per thread
+struct TileCfg {
+    int tx, tyt, nr;
+};
+constexpr TileCfg kTileCfgs[LBM_TILE_CONFIGS] = {{32, 8, 2}, {32, 4, 4}, {32, 8, 1}, {64, 4, 2}, {32, 16, 1}};
 constexpr int T3X = 32, T3Y = 8, T3Z = 32;   // D3Q19: 32 x 8 column, 32-plane z chunk (z-marching)
 
 void build_tiles(lbm_h h)
@@ -610,16 +617,29 @@ int check_planes(lbm_h h)
 int check_tiles(lbm_h h)
 {
     if (h->D == 3) return check_planes(h);
-    const int TX = T2X, TY = T2Y, TZ = 1;
-    const int T[3] = {TX, TY, TZ};
-    for (int l = 0; l < h->nl; l++) {
-        const Level &v = h->lev[l];
-        for (size_t t = 0; t < v.tile_flag.size(); t++) {
-            const int bx = (int)(t % v.tiles[0]), by = (int)((t / v.tiles[0]) % v.tiles[1]);
-            const int bz = (int)(t / ((size_t)v.tiles[0] * v.tiles[1]));
-            const int t0[3] = {bx * TX, by * TY, bz * TZ};
-            if (geometric_class(h, l, t0, T) != v.tile_flag[t])
-                return fail(nullptr, LBM_ERR_BAD_DESC, "internal: tile %zu of level %d classified inconsistently", t, l);
+    for (int c = 0; c < LBM_TILE_CONFIGS; c++) {
+        const int TX = kTileCfgs[c].tx, TY = kTileCfgs[c].tyt * kTileCfgs[c].nr;
+        const int T[3] = {TX, TY, 1};
+        for (int l = 0; l < h->nl; l++) {
+            const Level &v = h->lev[l];
+            const int tx = (int)((v.n[0] + TX - 1) / TX), ty = (int)((v.n[1] + TY - 1) / TY);
+            for (int by = 0; by < ty; by++)
+                for (int bx = 0; bx < tx; bx++) {
+                    const int x0 = bx * TX, y0 = by * TY;
+                    const int t0[3] = {x0, y0, 0};
+                    // node-by-node class of this tile
+                    bool any = false, fast = x0 - 2 >= 0 && x0 + TX + 2 <= v.n[0] && y0 - 2 >= 0 && y0 + TY + 2 <= v.n[1];
+                    for (int64_t y = y0; y < std::min<int64_t>(y0 + TY, v.n[1]); y++)
+                        for (int64_t x = x0; x < std::min<int64_t>(x0 + TX, v.n[0]); x++)
+                            any = any || v.cls[x + v.n[0] * y] != LBM_NODE_HOLE;
+                    for (int64_t y = y0 - 2; fast && y < y0 + TY + 2; y++)
+                        for (int64_t x = x0 - 2; fast && x < x0 + TX + 2; x++)
+                            fast = v.cls[x + v.n[0] * y] == LBM_NODE_BULK;
+                    const unsigned char want = !any ? TILE_SKIP : (fast ? TILE_FAST : TILE_GENERAL);
+                    if (geometric_class(h, l, t0, T) != want)
+                        return fail(nullptr, LBM_ERR_BAD_DESC, "internal: tile (%d,%d) of level %d, shape %d, "
+                                    "classified inconsistently", bx, by, l, c);
+                }
         }
     }
     return LBM_OK;
@@ -749,6 +769,29 @@ LevelDev level_dev(const lbm_h h, int l)
 }
 
 // ------------------------------------------------------------------ schedule
+template <int Q, typename S, int TX, int TYT, int NR>
+void launch_bulk2d_cfg(lbm_h h, int l, const void *src, void *dst, typename St<S>::R tau, typename St<S>::R om,
+                       typename St<S>::R sig, typename St<S>::R sps)
+{
+    const Level &v = h->lev[l];
+    const dim3 grid((unsigned)((v.n[0] + TX - 1) / TX), (unsigned)((v.n[1] + TYT * NR - 1) / (TYT * NR)), 1);
+    k_bulk2d<Q, S, TX, TYT, NR><<<grid, TX * TYT, 0, h->stream>>>(level_dev(h, l), (const S *)src, (S *)dst, tau, om,
+                                                                 sig, sps);
+}
+
+template <int Q, typename S>
+void launch_bulk2d(lbm_h h, int l, int cfg, const void *src, void *dst, typename St<S>::R tau,
+                   typename St<S>::R om, typename St<S>::R sig, typename St<S>::R sps)
+{
+    switch (cfg) {
+    case 1: launch_bulk2d_cfg<Q, S, 32, 4, 4>(h, l, src, dst, tau, om, sig, sps); break;
+    case 2: launch_bulk2d_cfg<Q, S, 32, 8, 1>(h, l, src, dst, tau, om, sig, sps); break;
+    case 3: launch_bulk2d_cfg<Q, S, 64, 4, 2>(h, l, src, dst, tau, om, sig, sps); break;
+    case 4: launch_bulk2d_cfg<Q, S, 32, 16, 1>(h, l, src, dst, tau, om, sig, sps); break;
+    default: launch_bulk2d_cfg<Q, S, 32, 8, 2>(h, l, src, dst, tau, om, sig, sps); break;
+    }
+}
+
 template <int Q, typename S>
 struct Sched {
     static void bulk(lbm_h h, int l, const void *src, void *dst)
@@ -769,8 +812,7 @@ struct Sched {
         using R = typename St<S>::R;
         const R tau = (R)v.tau, om = (R)(1.0 - 1.0 / v.tau), sig = (R)h->d.sigma, sps = (R)spsi;
         if constexpr (Lat<Q>::D == 2)
-            k_bulk2d<Q, S, T2X, T2YT, T2NR><<<nt, T2X * T2YT, 0, h->stream>>>(level_dev(h, l), (const S *)src,
-                                                                             (S *)dst, tau, om, sig, sps);
+            launch_bulk2d<Q, S>(h, l, v.tile_cfg, src, dst, tau, om, sig, sps);
         else
             k_bulk3d<Q, S, T3X, T3Y, T3Z><<<nt, T3X * T3Y, 0, h->stream>>>(level_dev(h, l), (const S *)src, (S *)dst,
                                                                           tau, om, sig, sps);
@@ -1691,6 +1733,76 @@ int lbm_load_state(lbm_h h, const void *buf, size_t len)
         CK(cudaMemcpy(I.hist_m, p, bm, cudaMemcpyHostToDevice));
         p += bm;
     }
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+
+// ================================================================== autotuner
+extern "C" {
+
+int lbm_set_tile_config(lbm_h h, int level, int cfg)
+{
+    if (!check_level(h, level)) return LBM_ERR_ARG;
+    if (cfg < 0 || cfg >= LBM_TILE_CONFIGS) return fail(h, LBM_ERR_ARG, "tile configuration %d out of range", cfg);
+    if (h->D != 2) return fail(h, LBM_ERR_ARG, "tile configurations apply to D2Q9 levels");
+    if (h->lev[level].tile_cfg != cfg) {
+        for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);  // graphs bake the launch shapes
+        h->graphs.clear();
+        h->graph_launches.clear();
+    }
+    h->lev[level].tile_cfg = cfg;
+    return LBM_OK;
+}
+
+int lbm_get_tile_config(lbm_h h, int level, int *cfg)
+{
+    if (!check_level(h, level)) return LBM_ERR_ARG;
+    if (!cfg) return fail(h, LBM_ERR_ARG, "cfg is NULL");
+    *cfg = h->lev[level].tile_cfg;
+    return LBM_OK;
+}
+
+int lbm_autotune(lbm_h h, int reps, double *us_out)
+{
+    if (!h || h->batch || !h->members.empty()) return h ? fail(h, LBM_ERR_ARG, "autotune single hierarchies") : LBM_ERR_ARG;
+    if (reps < 1 || reps > 10000) return fail(h, LBM_ERR_ARG, "reps must be in [1, 10000]");
+    if (h->D != 2) return LBM_OK;  // one 3-D shape
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int l = 0; l < h->nl; l++) {
+        Level &v = h->lev[l];
+        const long long k = h->ncoarse << l;
+        const void *src = v.f[k & 1];
+        void *dst = v.f[(k + 1) & 1];  // the state stays in src: timing does not advance it
+        double best = 1e300;
+        int best_c = 0;
+        for (int c = 0; c < LBM_TILE_CONFIGS; c++) {
+            const int saved = v.tile_cfg;
+            v.tile_cfg = c;
+            dispatch(h, [&](auto s) { decltype(s)::bulk(h, l, src, dst); });  // warm-up
+            CK(cudaEventRecord(e0, h->stream));
+            for (int r = 0; r < reps; r++) dispatch(h, [&](auto s) { decltype(s)::bulk(h, l, src, dst); });
+            CK(cudaEventRecord(e1, h->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            v.tile_cfg = saved;
+            const double us = 1e3 * ms / reps;
+            if (us_out) us_out[l * LBM_TILE_CONFIGS + c] = us;
+            if (us < best) {
+                best = us;
+                best_c = c;
+            }
+        }
+        const int rc = lbm_set_tile_config(h, l, best_c);
+        if (rc != LBM_OK) return rc;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaGetLastError());
     return LBM_OK;
 }
 

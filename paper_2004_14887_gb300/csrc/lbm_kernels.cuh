@@ -524,7 +524,7 @@ __device__ __forceinline__ void reg_moments(const R (&f)[Q], R &rho, R *u)
             if (L::c(i, a) != 0) m[a] += R(L::c(i, a)) * f[i];
     }
     rho = r;
-    const R inv = R(1) / r;
+    const R inv = recip(r);
 #pragma unroll
     for (int a = 0; a < D; a++) u[a] = m[a] * inv;
 }
@@ -747,7 +747,7 @@ __device__ __forceinline__ void bulk2d_tile(const LevelDev &Lv, const S *__restr
 }
 
 template <int Q, typename S, int TX, int TYT, int NR>
-__global__ void __launch_bounds__(TX *TYT, sizeof(S) == 8 ? 1 : 4) k_bulk2d(LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
+__global__ void __launch_bounds__(TX *TYT, sizeof(S) == 8 ? 1 : (TX * TYT >= 256 ? 1024 / (TX * TYT) : 4)) k_bulk2d(LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
                                                      typename St<S>::R tau, typename St<S>::R om,
                                                      typename St<S>::R sigma, typename St<S>::R spsi)
 {

@@ -58,7 +58,9 @@ EXPORTS = [
     "lbm_timing_enable", "lbm_timing_read", "lbm_launch_count", "lbm_device_bytes", "lbm_synchronize",
     "lbm_last_error", "lbm_destroy", "lbm_reduce_static", "lbm_create_batch", "lbm_batch_member",
     "lbm_batch_check_barrier", "lbm_set_probes", "lbm_get_probes", "lbm_save_state", "lbm_load_state",
+    "lbm_autotune", "lbm_set_tile_config", "lbm_get_tile_config",
 ]
+TILE_CONFIGS = 5
 
 _lib = None
 
@@ -103,6 +105,9 @@ def lib():
     L.lbm_get_probes.argtypes = [vp, dp, i64p]
     L.lbm_save_state.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
     L.lbm_load_state.argtypes = [vp, vp, C.c_size_t]
+    L.lbm_autotune.argtypes = [vp, C.c_int, dp]
+    L.lbm_set_tile_config.argtypes = [vp, C.c_int, C.c_int]
+    L.lbm_get_tile_config.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
     _lib = L
     return L
 
@@ -303,6 +308,41 @@ class Hierarchy:
     def load_state(self, buf):
         buf = np.ascontiguousarray(buf, dtype=np.uint8)
         self._check(lib().lbm_load_state(self._h, buf.ctypes.data_as(C.c_void_p), buf.size))
+
+    def set_tile_config(self, level, cfg):
+        self._check(lib().lbm_set_tile_config(self._h, level, int(cfg)))
+
+    def tile_config(self, level):
+        c = C.c_int()
+        self._check(lib().lbm_get_tile_config(self._h, level, C.byref(c)))
+        return c.value
+
+    def autotune(self, reps=20, cache=None):
+        """Pick the fastest bulk tile shape per level (lbm_autotune).  With `cache` (a
+        JSON file path) results are looked up by (lattice, storage, level boxes) and
+        stored after a measurement."""
+        import json
+
+        key = json.dumps([self.q, self._desc.storage, [lv["n"] for lv in self.levels]])
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as fh:
+                table = json.load(fh)
+            if key in table:
+                for l, c in enumerate(table[key]["cfg"]):
+                    self.set_tile_config(l, c)
+                return table[key]
+        us = (C.c_double * (self.n_levels * TILE_CONFIGS))()
+        self._check(lib().lbm_autotune(self._h, int(reps), us))
+        res = {"cfg": [self.tile_config(l) for l in range(self.n_levels)],
+               "us": [list(us[l * TILE_CONFIGS:(l + 1) * TILE_CONFIGS]) for l in range(self.n_levels)]}
+        if cache:
+            table[key] = res
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as fh:
+                json.dump(table, fh)
+            os.replace(tmp, cache)
+        return res
 
     def max_newton_iters(self):
         return lib().lbm_max_newton_iters(self._h)
