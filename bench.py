@@ -381,6 +381,34 @@ def run_gb300(args):
             if st in vals and "f64" in vals:
                 variants[f"{st}_speedup_vs_f64"] = vals[st]["value"] / vals["f64"]["value"]
 
+    # the same bulk kernel on one large level (4096^2, 1.2 GB per launch in FP32): where
+    # the step is long enough for HBM to be the limit, away from launch latency
+    scale = None
+    if not args.no_scale_check and L > 0 and h.q == 9:
+        n = 4096
+        ds = {"lattice": 9, "coarse_n": (n, n), "boxes": [], "nu0": 1e-5, "storage": main_storage,
+              "init": {"kind": "vortex", "xc": n / 2, "yc": n / 2, "Rc": n / 16, "swirl": 0.05, "U": (0.05, 0.02, 0.0)}}
+        hs = lbm.Hierarchy(ds)
+        r, u = W.init_fields(ds, 0)
+        hs.init_fields(0, r, u)
+        if not args.no_autotune:
+            hs.autotune(reps=5)
+        hs.advance(3)
+        torch.cuda.synchronize()
+        ks = 20
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        hs.advance(ks)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_s = e0.elapsed_time(e1) / ks
+        bytes_s = n * n * 2 * h.q * BYTES_PER_POP[main_storage]
+        scale = {"workload": f"single periodic D2Q9 level {n}^2, {main_storage}, vortex", "ms_per_launch": ms_s,
+                 "achieved_gbs": bytes_s / (ms_s * 1e-3) / 1e9, "frac": bytes_s / (ms_s * 1e-3) / 1e9 / _peaks()[0],
+                 "mlups": n * n / (ms_s * 1e-3) / 1e6}
+        hs.close()
+        del hs
+
     # end to end through the public API with host buffers: init (H2D), K steps, macros (D2H)
     e2e = None
     if not args.no_e2e:
@@ -433,6 +461,7 @@ def run_gb300(args):
         "clocks": clocks,
         "e2e": e2e,
         "variants": variants,
+        "bulk_at_scale": scale,
     }
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
@@ -517,6 +546,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-scale-check", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
