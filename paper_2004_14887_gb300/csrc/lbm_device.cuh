@@ -18,6 +18,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+#include <utility>
+
 namespace lbmg {
 
 enum : int { ST_NEWTON = 1, ST_NAN = 2, ST_TIMEOUT = 4 };
@@ -58,6 +61,19 @@ template <> struct Lat<19> {
         return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
     }
 };
+
+// compile-time loop: f(std::integral_constant<int, i>) for i = 0..N-1, so that every
+// lattice constant used inside is a constant expression
+template <typename F, int... I>
+__host__ __device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, I...>)
+{
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__host__ __device__ __forceinline__ void static_for(F &&f)
+{
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
 
 // symmetric tensors: 0 xx, 1 yy, 2 zz, 3 xy, 4 xz, 5 yz
 __host__ __device__ constexpr int sym_index(int a, int b)
@@ -239,15 +255,21 @@ __device__ __forceinline__ void hrr_collide(R (&f)[Q], R rho, const R *u, const 
     const R cs2 = R(1) / R(3);
     R Pi[6] = {0, 0, 0, 0, 0, 0};
     R fsum = R(0);
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
+    static_for<Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
         fsum += f[i];
-#pragma unroll
-        for (int a = 0; a < D; a++)
-#pragma unroll
-            for (int b = a; b < D; b++)
-                if (L::c(i, a) * L::c(i, b) != 0) Pi[sym_index(a, b)] += R(L::c(i, a) * L::c(i, b)) * f[i];
-    }
+        static_for<D>([&](auto ac) {
+            constexpr int a = decltype(ac)::value;
+            static_for<D>([&](auto bc) {
+                constexpr int b = decltype(bc)::value;
+                constexpr int p = L::c(i, a) * L::c(i, b);
+                if constexpr (b >= a && p != 0) {
+                    if constexpr (p > 0) Pi[sym_index(a, b)] += f[i];
+                    else Pi[sym_index(a, b)] -= f[i];
+                }
+            });
+        });
+    });
     const R kfd = R(-2) * tau * rho * cs2;
     R B[6], A[6];
 #pragma unroll
@@ -270,28 +292,31 @@ __device__ __forceinline__ void hrr_collide(R (&f)[Q], R rho, const R *u, const 
     R trB = R(0);
 #pragma unroll
     for (int a = 0; a < D; a++) trB += B[sym_index(a, a)];
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        R cu = R(0), h2 = R(0), h3 = R(0);
-#pragma unroll
-        for (int a = 0; a < D; a++)
-            if (L::c(i, a) != 0) cu += R(L::c(i, a)) * u[a];
-#pragma unroll
-        for (int a = 0; a < D; a++) {
-            if (L::c(i, a) != 0) h2 += B[sym_index(a, a)];
-#pragma unroll
-            for (int b = a + 1; b < D; b++)
-                if (L::c(i, a) * L::c(i, b) != 0) h2 += R(2 * L::c(i, a) * L::c(i, b)) * B[sym_index(a, b)];
-        }
-        h2 -= cs2 * trB;
-#pragma unroll
-        for (int a = 0; a < D; a++)
-#pragma unroll
-            for (int b = 0; b < D; b++)
-                if (a != b && L::c(i, b) != 0)
-                    h3 += (R(L::c(i, a) * L::c(i, a)) - cs2) * R(L::c(i, b)) * T[a][b];
-        f[i] = R(L::w(i)) * (rho + R(3) * rho * cu + R(4.5) * h2 + R(13.5) * h3);
-    }
+    const R base = rho, r3 = R(3) * rho, ctr = cs2 * trB;
+    static_for<Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        R cu = R(0), h2 = -ctr, h3 = R(0);
+        static_for<D>([&](auto ac) {
+            constexpr int a = decltype(ac)::value;
+            constexpr int ca = L::c(i, a);
+            if constexpr (ca != 0) {
+                if constexpr (ca > 0) cu += u[a];
+                else cu -= u[a];
+                h2 += B[sym_index(a, a)];
+            }
+            static_for<D>([&](auto bc) {
+                constexpr int b = decltype(bc)::value;
+                constexpr int cb = L::c(i, b);
+                if constexpr (b > a && ca * cb != 0) h2 += R(2 * ca * cb) * B[sym_index(a, b)];
+                // H3_aab = (c_a^2 - cs2) c_b, for a != b and c_b != 0
+                if constexpr (a != b && cb != 0) {
+                    constexpr double k3 = ((double)(ca * ca) - 1.0 / 3.0) * cb;
+                    h3 += R(k3) * T[a][b];
+                }
+            });
+        });
+        f[i] = R(L::w(i)) * (base + r3 * cu + R(4.5) * h2 + R(13.5) * h3);
+    });
 }
 
 // Equilibrium of Eq. (fEq_herm) of population i

@@ -516,13 +516,15 @@ __device__ __forceinline__ void reg_moments(const R (&f)[Q], R &rho, R *u)
     using L = Lat<Q>;
     constexpr int D = L::D;
     R r = R(0), m[3] = {R(0), R(0), R(0)};
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
+    static_for<Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
         r += f[i];
-#pragma unroll
-        for (int a = 0; a < D; a++)
-            if (L::c(i, a) != 0) m[a] += R(L::c(i, a)) * f[i];
-    }
+        static_for<D>([&](auto ac) {
+            constexpr int a = decltype(ac)::value;
+            if constexpr (L::c(i, a) > 0) m[a] += f[i];
+            else if constexpr (L::c(i, a) < 0) m[a] -= f[i];
+        });
+    });
     rho = r;
     const R inv = recip(r);
 #pragma unroll
@@ -583,8 +585,10 @@ __device__ __forceinline__ void collide_store(const LevelDev &Lv, typename St<S>
         }
     }
     hrr_collide<Q, R>(f, rho, u, Sv, Cv, tau, om, sigma, spsi);
-#pragma unroll
-    for (int i = 0; i < Q; i++) St<S>::st(fdst + (long long)i * Lv.g.pitch, idx, f[i], L::w(i));
+    static_for<Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        St<S>::st(fdst + (long long)i * Lv.g.pitch, idx, f[i], L::w(i));
+    });
 }
 
 // 2-D: one CTA per tile of TX x (TYT*NR) nodes, TX x TYT threads, NR nodes per thread
@@ -796,8 +800,8 @@ __device__ __forceinline__ int general_pull(const LevelDev &Lv, const S *__restr
     const bool ok = wrap_coord(x, g.n[0], g.per[0]) && wrap_coord(y, g.n[1], g.per[1]) && wrap_coord(z, g.n[2], g.per[2]);
     const int tag = ok ? Lv.tag[box_index(g, x, y, z)] : TAG_HOLE;
     const R *pop = (const R *)Lv.if_pop;
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
+    static_for<Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
         // bulk sources are nodes: a one-step wrap on periodic axes is all they need
         int sx = x - L::c(i, 0), sy = y - L::c(i, 1), sz = z - L::c(i, 2);
         sx += (sx < 0) ? g.n[0] : ((sx >= g.n[0]) ? -g.n[0] : 0);
@@ -805,7 +809,7 @@ __device__ __forceinline__ int general_pull(const LevelDev &Lv, const S *__restr
         sz += (sz < 0) ? g.n[2] : ((sz >= g.n[2]) ? -g.n[2] : 0);
         f[i] = tag == TAG_BULK ? St<S>::ld(fsrc + (long long)i * g.pitch, box_index(g, sx, sy, sz), L::w(i))
                                : (tag >= 0 ? pop[(long long)i * Lv.nif + tag] : R(0));
-    }
+    });
     return tag;
 }
 
@@ -884,17 +888,17 @@ __global__ void __launch_bounds__(TX *TY) k_bulk3d(LevelDev Lv, const S *__restr
             tag = TAG_BULK;
             htag = hb >= 0 ? TAG_BULK : TAG_HOLE;
             const int idx = x + g.n[0] * y + n01 * p, hidx = qx + g.n[0] * qy + n01 * p;
-#pragma unroll
-            for (int i = 0; i < Q; i++) {
+            static_for<Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
                 const int off = L::c(i, 0) + g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
                 f[i] = St<S>::ld(fsrc + (long long)i * g.pitch, idx - off, L::w(i));
-            }
+            });
             if (hb >= 0) {
-#pragma unroll
-                for (int i = 0; i < Q; i++) {
+                static_for<Q>([&](auto ic) {
+                    constexpr int i = decltype(ic)::value;
                     const int off = L::c(i, 0) + g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
                     fh[i] = St<S>::ld(fsrc + (long long)i * g.pitch, hidx - off, L::w(i));
-                }
+                });
             }
         } else if (cls == LOAD_GENERAL) {
             tag = general_pull<Q, S>(Lv, fsrc, x, y, p, f);
@@ -973,8 +977,10 @@ __global__ void __launch_bounds__(TX *TY) k_bulk3d(LevelDev Lv, const S *__restr
             }
             R rho = s_rho[s0][hs], u[3] = {s_u[s0][0][hs], s_u[s0][1][hs], s_u[s0][2][hs]};
             hrr_collide<Q, R>(fc, rho, u, Sv, Cv, tau, om, sigma, spsi);
-#pragma unroll
-            for (int i = 0; i < Q; i++) St<S>::st(fdst + (long long)i * g.pitch, idx, fc[i], L::w(i));
+            static_for<Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                St<S>::st(fdst + (long long)i * g.pitch, idx, fc[i], L::w(i));
+            });
         }
 #pragma unroll
         for (int i = 0; i < Q; i++) fc[i] = fn[i];
