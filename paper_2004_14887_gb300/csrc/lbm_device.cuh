@@ -114,8 +114,10 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 struct LevelGeo {
     int n[3];
     int per[3];
-    long long N;      // box nodes
-    long long pitch;  // elements between population planes
+    int px;           // row pitch in slots: n[0] padded to a multiple of 8
+    long long N;      // box nodes n[0] n[1] n[2] (dense order of the host arrays)
+    long long NS;     // slots px n[1] n[2] of the tag map and population planes
+    long long pitch;  // elements between population planes (>= NS)
 };
 
 struct LevelDev {
@@ -143,19 +145,6 @@ struct LevelDev {
     const double *ie_w;
 };
 
-__device__ __forceinline__ long long node_index(const LevelGeo &g, int x, int y, int z)
-{
-    return (long long)x + (long long)g.n[0] * ((long long)y + (long long)g.n[1] * z);
-}
-
-__device__ __forceinline__ void node_coords(const LevelGeo &g, long long idx, int &x, int &y, int &z)
-{
-    x = (int)(idx % g.n[0]);
-    long long r = idx / g.n[0];
-    y = (int)(r % g.n[1]);
-    z = (int)(r / g.n[1]);
-}
-
 // wrap (periodic) or reject a coordinate; returns false outside a non-periodic box
 __device__ __forceinline__ bool wrap_coord(int &v, int n, int per)
 {
@@ -166,17 +155,11 @@ __device__ __forceinline__ bool wrap_coord(int &v, int n, int per)
     return true;
 }
 
-// index of node (x,y,z) displaced by (dx,dy,dz), -1 if outside a non-periodic box
-__device__ __forceinline__ long long shifted_index(const LevelGeo &g, long long idx, int dx, int dy, int dz)
+// slot of the node with dense index idx (x fastest over n[0], n[1], n[2])
+__device__ __forceinline__ long long dense_to_slot(const LevelGeo &g, long long idx)
 {
-    int x, y, z;
-    node_coords(g, idx, x, y, z);
-    x += dx;
-    y += dy;
-    z += dz;
-    if (!wrap_coord(x, g.n[0], g.per[0]) || !wrap_coord(y, g.n[1], g.per[1]) || !wrap_coord(z, g.n[2], g.per[2]))
-        return -1;
-    return node_index(g, x, y, z);
+    const long long x = idx % g.n[0], yz = idx / g.n[0];
+    return x + (long long)g.px * yz;
 }
 
 // ------------------------------------------------------------------ H-RR physics

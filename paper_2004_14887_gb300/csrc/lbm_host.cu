@@ -32,7 +32,8 @@ struct DevBuf {
 struct Level {
     int64_t n[3] = {1, 1, 1}, off[3] = {0, 0, 0};
     int per[3] = {1, 1, 1};
-    long long N = 0, pitch = 0;
+    long long N = 0, pitch = 0;  // dense node count; elements between population planes
+    long long px = 1, NS = 0;     // row pitch (x extent padded to 8 nodes) and box slots px*ny*nz
     double tau = 0.5;
     std::vector<uint8_t> cls;
     std::vector<int> tag;
@@ -258,7 +259,11 @@ int build_geometry(lbm_h h)
             if (all_span) return fail(nullptr, LBM_ERR_BAD_DESC, "level %d spans every axis: refine level 0 instead", l);
         }
         v.N = (long long)v.n[0] * v.n[1] * v.n[2];
-        v.pitch = (v.N + 31) / 32 * 32;
+        // rows padded to 8 nodes: every row starts 16-byte aligned in each storage type
+        // (bulk tensor copies need 16-byte strides); padding slots are holes
+        v.px = (v.n[0] + 7) / 8 * 8;
+        v.NS = v.px * v.n[1] * v.n[2];
+        v.pitch = (v.NS + 31) / 32 * 32;
         v.tau = l == 0 ? 0.5 + 3.0 * d.nu0 : 2.0 * h->lev[l - 1].tau - 0.5;
         if (l + 1 < h->nl) {
             v.has_child = true;
@@ -680,7 +685,15 @@ int upload_all(lbm_h h)
             v.f[k] = dev_alloc(h, (size_t)Q * v.pitch * ss);
             if (!v.f[k]) return fail(h, LBM_ERR_OOM, "population buffer of level %d (%zu bytes)", l, (size_t)Q * v.pitch * ss);
         }
-        v.d_tag = upload(h, v.tag, &ok);
+        {
+            // device tag map in the padded slot layout
+            std::vector<int> slot_tag((size_t)v.NS, TAG_HOLE);
+            for (long long idx = 0; idx < v.N; idx++) {
+                const long long x = idx % v.n[0], yz = idx / v.n[0];
+                slot_tag[(size_t)(x + v.px * yz)] = v.tag[(size_t)idx];
+            }
+            v.d_tag = upload(h, slot_tag, &ok);
+        }
         const size_t ni = std::max(1, v.nif), as = arith_size(h->d.storage);
         v.if_pop = dev_alloc(h, ni * Q * as);
         v.if_mac = dev_alloc(h, ni * 4 * as);
@@ -739,6 +752,8 @@ LevelDev level_dev(const lbm_h h, int l)
         d.tiles[a] = v.tiles[a];
     }
     d.g.N = v.N;
+    d.g.px = (int)v.px;
+    d.g.NS = v.NS;
     d.g.pitch = v.pitch;
     d.f[0] = v.f[0];
     d.f[1] = v.f[1];
@@ -1604,7 +1619,7 @@ int lbm_set_probes(lbm_h h, int n, const double *xyz, int64_t capacity)
                 const long long id = node_of(h, l, p);
                 if (id < 0) ok = false;
                 else {
-                    idx[c] = (int)id;
+                    idx[c] = (int)(id % v.n[0] + v.px * (id / v.n[0]));  // slot of the node
                     ww[c] = wc;
                 }
             }

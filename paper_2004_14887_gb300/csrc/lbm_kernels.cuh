@@ -38,7 +38,7 @@ struct TimeW {
 
 __device__ __forceinline__ int box_index(const LevelGeo &g, int x, int y, int z)
 {
-    return x + g.n[0] * (y + g.n[1] * z);
+    return x + g.px * (y + g.n[1] * z);
 }
 
 // index of (x,y,z) + (dx,dy,dz) with periodic wrap, -1 off a non-periodic box
@@ -650,25 +650,25 @@ __device__ __forceinline__ void bulk2d_tile(const LevelDev &Lv, const S *__restr
     for (int r = 0; r < NR; r++) {
         const int y = Y0 + tr + r * TYT;
         inside[r] = x < g.n[0] && y < g.n[1];
-        idx[r] = x + g.n[0] * y;
+        idx[r] = x + g.px * y;
     }
     int otag[NR];
     if (flag == TILE_FAST) {
 #pragma unroll
         for (int r = 0; r < NR; r++) otag[r] = TAG_BULK;
         htag = hb >= 0 ? TAG_BULK : TAG_HOLE;
-        const int hidx = (X0 + hx - 1) + g.n[0] * (Y0 + hy - 1);
+        const int hidx = (X0 + hx - 1) + g.px * (Y0 + hy - 1);
 #pragma unroll
         for (int i = 0; i < Q; i++) {
             const S *pi = fsrc + (long long)i * g.pitch;  // population plane
-            const int off = L::c(i, 0) + g.n[0] * L::c(i, 1);
+            const int off = L::c(i, 0) + g.px * L::c(i, 1);
 #pragma unroll
             for (int r = 0; r < NR; r++) f[r][i] = St<S>::ld(pi, idx[r] - off, L::w(i));
         }
         if (hb >= 0) {
 #pragma unroll
             for (int i = 0; i < Q; i++) {
-                const int off = L::c(i, 0) + g.n[0] * L::c(i, 1);
+                const int off = L::c(i, 0) + g.px * L::c(i, 1);
                 fh[i] = St<S>::ld(fsrc + (long long)i * g.pitch, hidx - off, L::w(i));
             }
         }
@@ -681,11 +681,11 @@ __device__ __forceinline__ void bulk2d_tile(const LevelDev &Lv, const S *__restr
             ox[r] = x;
             oy[r] = Y0 + tr + r * TYT;
             const bool ok = wrap_coord(ox[r], g.n[0], g.per[0]) && wrap_coord(oy[r], g.n[1], g.per[1]);
-            otag[r] = ok ? Lv.tag[ox[r] + g.n[0] * oy[r]] : TAG_HOLE;
+            otag[r] = ok ? Lv.tag[ox[r] + g.px * oy[r]] : TAG_HOLE;
         }
         int qx = X0 + hx - 1, qy = Y0 + hy - 1;
         const bool hvalid = hb >= 0 && wrap_coord(qx, g.n[0], g.per[0]) && wrap_coord(qy, g.n[1], g.per[1]);
-        htag = hvalid ? Lv.tag[qx + g.n[0] * qy] : TAG_HOLE;
+        htag = hvalid ? Lv.tag[qx + g.px * qy] : TAG_HOLE;
         const R *pop = (const R *)Lv.if_pop;
 #pragma unroll
         for (int i = 0; i < Q; i++) {
@@ -696,13 +696,13 @@ __device__ __forceinline__ void bulk2d_tile(const LevelDev &Lv, const S *__restr
                 int sx = ox[r] - L::c(i, 0), sy = oy[r] - L::c(i, 1);
                 sx += (sx < 0) ? g.n[0] : ((sx >= g.n[0]) ? -g.n[0] : 0);
                 sy += (sy < 0) ? g.n[1] : ((sy >= g.n[1]) ? -g.n[1] : 0);
-                f[r][i] = otag[r] == TAG_BULK ? St<S>::ld(pi, sx + g.n[0] * sy, L::w(i))
+                f[r][i] = otag[r] == TAG_BULK ? St<S>::ld(pi, sx + g.px * sy, L::w(i))
                                               : (otag[r] >= 0 ? pop[(long long)i * Lv.nif + otag[r]] : R(0));
             }
-            int px = qx - L::c(i, 0), py = qy - L::c(i, 1);
-            px += (px < 0) ? g.n[0] : ((px >= g.n[0]) ? -g.n[0] : 0);
-            py += (py < 0) ? g.n[1] : ((py >= g.n[1]) ? -g.n[1] : 0);
-            fh[i] = htag == TAG_BULK ? St<S>::ld(pi, px + g.n[0] * py, L::w(i))
+            int hsx = qx - L::c(i, 0), hsy = qy - L::c(i, 1);
+            hsx += (hsx < 0) ? g.n[0] : ((hsx >= g.n[0]) ? -g.n[0] : 0);
+            hsy += (hsy < 0) ? g.n[1] : ((hsy >= g.n[1]) ? -g.n[1] : 0);
+            fh[i] = htag == TAG_BULK ? St<S>::ld(pi, hsx + g.px * hsy, L::w(i))
                                      : (htag >= 0 ? pop[(long long)i * Lv.nif + htag] : R(0));
         }
     }
@@ -875,7 +875,7 @@ __global__ void __launch_bounds__(TX *TY) k_bulk3d(LevelDev Lv, const S *__restr
         hb = hx + HX * hy;
     }
     const int qx = X0 + hx - 1, qy = Y0 + hy - 1;
-    const int n01 = g.n[0] * g.n[1];
+    const int n01 = g.px * g.n[1];
 
     // pull plane p into (f, tag) for the own node and the macros of own and halo nodes
     // into ring slot p mod 3
@@ -887,16 +887,16 @@ __global__ void __launch_bounds__(TX *TY) k_bulk3d(LevelDev Lv, const S *__restr
         if (cls == LOAD_FAST) {
             tag = TAG_BULK;
             htag = hb >= 0 ? TAG_BULK : TAG_HOLE;
-            const int idx = x + g.n[0] * y + n01 * p, hidx = qx + g.n[0] * qy + n01 * p;
+            const int idx = x + g.px * y + n01 * p, hidx = qx + g.px * qy + n01 * p;
             static_for<Q>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                const int off = L::c(i, 0) + g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
+                const int off = L::c(i, 0) + g.px * L::c(i, 1) + n01 * L::c(i, 2);
                 f[i] = St<S>::ld(fsrc + (long long)i * g.pitch, idx - off, L::w(i));
             });
             if (hb >= 0) {
                 static_for<Q>([&](auto ic) {
                     constexpr int i = decltype(ic)::value;
-                    const int off = L::c(i, 0) + g.n[0] * L::c(i, 1) + n01 * L::c(i, 2);
+                    const int off = L::c(i, 0) + g.px * L::c(i, 1) + n01 * L::c(i, 2);
                     fh[i] = St<S>::ld(fsrc + (long long)i * g.pitch, hidx - off, L::w(i));
                 });
             }
@@ -932,7 +932,7 @@ __global__ void __launch_bounds__(TX *TY) k_bulk3d(LevelDev Lv, const S *__restr
         if (tc != TAG_HOLE) {
             const int sm = (z + 2) % 3, s0 = z % 3, sp = (z + 1) % 3;  // planes z-1, z, z+1
             R Sv[6], Cv[6];
-            const int idx = x + g.n[0] * y + n01 * z;
+            const int idx = x + g.px * y + n01 * z;
             if (tc == TAG_BULK) {
                 R nr[3][2], nu[3][2][3];
                 const int hh[2][2] = {{hs + 1, hs - 1}, {hs + HX, hs - HX}};
@@ -1203,13 +1203,14 @@ __global__ void k_init(LevelGeo g, const int *__restrict__ tag, const double *__
     constexpr int D = L::D;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= g.N) return;
-    const bool hole = tag[idx] == TAG_HOLE;
+    const long long sl = dense_to_slot(g, idx);
+    const bool hole = tag[sl] == TAG_HOLE;
     double uu[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < D; a++) uu[a] = u[(long long)a * g.N + idx];
     for (int i = 0; i < Q; i++) {
         const double v = hole ? L::w(i) : feq_one<Q>(i, rho[idx], uu);
-        St<S>::st(f0, (long long)i * g.pitch + idx, (typename St<S>::R)v, L::w(i));
-        St<S>::st(f1, (long long)i * g.pitch + idx, (typename St<S>::R)v, L::w(i));
+        St<S>::st(f0, (long long)i * g.pitch + sl, (typename St<S>::R)v, L::w(i));
+        St<S>::st(f1, (long long)i * g.pitch + sl, (typename St<S>::R)v, L::w(i));
     }
 }
 
@@ -1221,10 +1222,11 @@ __global__ void k_macros(LevelGeo g, const int *__restrict__ tag, const S *__res
     constexpr int D = L::D;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= g.N) return;
-    const bool hole = tag[idx] == TAG_HOLE;
+    const long long sl = dense_to_slot(g, idx);
+    const bool hole = tag[sl] == TAG_HOLE;
     double r = 0.0, m[3] = {0.0, 0.0, 0.0};
     for (int i = 0; i < Q; i++) {
-        const double v = hole ? 0.0 : (double)St<S>::ld(f, (long long)i * g.pitch + idx, L::w(i));
+        const double v = hole ? 0.0 : (double)St<S>::ld(f, (long long)i * g.pitch + sl, L::w(i));
         if (pops) pops[(long long)i * g.N + idx] = v;
         r += v;
         for (int a = 0; a < D; a++) m[a] += L::c(i, a) * v;
@@ -1246,10 +1248,11 @@ __global__ void k_reduce_partial(LevelGeo g, const int *__restrict__ tag, const 
     bool bad = false;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.N;
          idx += (long long)gridDim.x * blockDim.x) {
-        if (tag[idx] == TAG_HOLE) continue;
+        const long long sl = dense_to_slot(g, idx);
+        if (tag[sl] == TAG_HOLE) continue;
         const double w = wnode[idx];
         for (int i = 0; i < Q; i++) {
-            const double v = (double)St<S>::ld(f, (long long)i * g.pitch + idx, L::w(i));
+            const double v = (double)St<S>::ld(f, (long long)i * g.pitch + sl, L::w(i));
             if (!isfinite(v)) bad = true;
             acc[0] += w * v;
             for (int a = 0; a < D; a++) acc[1 + a] += w * L::c(i, a) * v;
