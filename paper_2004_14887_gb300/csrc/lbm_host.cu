@@ -3,6 +3,7 @@
 // tables, the recursive 2:1 sub-cycling schedule of Sec. 3.5 issued as kernel
 // launches (captured once per coarse-step phase into CUDA graphs), and the C-ABI
 // declared in include/lbm.h.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,6 +42,8 @@ struct Level {
     int tiles[3] = {1, 1, 1};
     int nTFP = 0, nIE = 0, nTFC = 0, nif = 0;
     int tile_cfg = 0;  // D2Q9 bulk tile shape (kTileCfgs), chosen by lbm_autotune
+    int zc = 1;        // D3Q19: planes per z chunk of the bulk kernel
+    CUtensorMap tmap[2];  // D3Q19: bulk tensor copy maps of f[0], f[1]
     int64_t n_active = 0;
     // child-box in this level's node coordinates, for volume weights
     bool has_child = false;
@@ -484,6 +487,7 @@ int build_interfaces(lbm_h h)
     return LBM_OK;
 }
 
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // bounded device waits: 2 s
 constexpr int T2X = 32, T2YT = 8, T2NR = 2;  // D2Q9 tile: 32 x 8 threads, 2 rows per thread
 constexpr int T2Y = T2YT * T2NR;
 
@@ -492,17 +496,20 @@ struct TileCfg {
     int tx, tyt, nr;
 };
 constexpr TileCfg kTileCfgs[LBM_TILE_CONFIGS] = {{32, 8, 2}, {32, 4, 4}, {32, 8, 1}, {64, 4, 2}, {32, 16, 1}};
-constexpr int T3X = 32, T3Y = 8, T3Z = 32;   // D3Q19: 32 x 8 column, 32-plane z chunk (z-marching)
+constexpr int T3X = 32, T3Y = 8;   // D3Q19: 32 x 8 columns marching in z (k_bulk3d)
+// D3Q19 z chunking the autotuner chooses from: target CTA waves per launch (a chunk of
+// fewer planes gives more CTAs; every chunk re-stages two planes)
+constexpr int kWaves3[LBM_TILE_CONFIGS] = {4, 2, 8, 1, 16};
 
 void build_tiles(lbm_h h)
 {
-    const int TX = h->D == 2 ? T2X : T3X, TY = h->D == 2 ? T2Y : T3Y, TZ = h->D == 2 ? 1 : T3Z;
+    const int TX = h->D == 2 ? T2X : T3X, TY = h->D == 2 ? T2Y : T3Y, TZ = 1;
     for (int l = 0; l < h->nl; l++) {
         Level &v = h->lev[l];
         v.tiles[0] = (int)((v.n[0] + TX - 1) / TX);
         v.tiles[1] = (int)((v.n[1] + TY - 1) / TY);
-        v.tiles[2] = (int)((v.n[2] + TZ - 1) / TZ);
-        if (h->D == 3) continue;  // 3-D columns are classified plane by plane (check_planes)
+        v.tiles[2] = 1;
+        if (h->D == 3) continue;  // 3-D columns are classified plane by plane (check_planes); chunks: plan_chunks
         const long long nt = (long long)v.tiles[0] * v.tiles[1] * v.tiles[2];
         v.tile_flag.assign(nt, TILE_GENERAL);
         const int rz = h->D == 3 ? 2 : 0;
@@ -674,6 +681,84 @@ std::vector<double> node_weights(const lbm_h h, int l)
     return w;
 }
 
+// ------------------------------------------------------------------ bulk tensor copies (D3Q19)
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_tiled()
+{
+    static std::once_flag once;
+    static EncodeTiled fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiled)p;
+    });
+    return fn;
+}
+
+// dynamic shared memory limit of the 3-D kernel for storage S; CTAs per SM
+template <typename S>
+int bulk3d_prepare(int *per_sm)
+{
+    using G = Stage3<19, S, T3X, T3Y>;
+    auto kern = k_bulk3d<19, S, T3X, T3Y>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes) != cudaSuccess)
+        return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, T3X * T3Y, G::smem_bytes) != cudaSuccess) return -1;
+    return 0;
+}
+
+// z chunk of a 3-D level: about kWaves3[cfg] waves of CTAs, chunks of at least 8 planes
+int plan_chunks(lbm_h h, int l)
+{
+    Level &v = h->lev[l];
+    int dev = 0, sms = 0, per_sm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int st = h->d.storage;
+    const int rc = st == LBM_F64 ? bulk3d_prepare<double>(&per_sm)
+                   : st == LBM_F32 ? bulk3d_prepare<float>(&per_sm)
+                                   : bulk3d_prepare<__half>(&per_sm);
+    if (rc != 0 || per_sm < 1) return fail(h, LBM_ERR_CUDA, "3-D bulk kernel does not fit an SM");
+    const long long cols = (long long)v.tiles[0] * v.tiles[1];
+    const long long want = (long long)kWaves3[v.tile_cfg] * sms * per_sm;
+    const long long nmax = std::max<long long>(1, v.n[2] / 8);
+    const long long nch = std::min<long long>(std::max<long long>(1, (want + cols - 1) / cols), nmax);
+    v.zc = (int)((v.n[2] + nch - 1) / nch);
+    v.tiles[2] = (int)((v.n[2] + v.zc - 1) / v.zc);
+    return LBM_OK;
+}
+
+// 4-D maps (x, y, z, population) of both population buffers of a 3-D level; the box is
+// one population over TX + 2 XA x TY + 4 nodes of one plane (Stage3)
+int make_tensor_maps(lbm_h h, int l)
+{
+    Level &v = h->lev[l];
+    EncodeTiled enc = encode_tiled();
+    if (!enc) return fail(h, LBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    const int st = h->d.storage;
+    const size_t es = store_size(st);
+    const int xa = 16 / (int)es;
+    const CUtensorMapDataType dt = st == LBM_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                   : st == LBM_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const cuuint64_t dims[4] = {(cuuint64_t)v.n[0], (cuuint64_t)v.n[1], (cuuint64_t)v.n[2], (cuuint64_t)h->Q};
+    const cuuint64_t strides[3] = {(cuuint64_t)(v.px * es), (cuuint64_t)(v.px * v.n[1] * es), (cuuint64_t)(v.pitch * es)};
+    const cuuint32_t box[4] = {(cuuint32_t)(T3X + 2 * xa), (cuuint32_t)(T3Y + 4), 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    for (int k = 0; k < 2; k++) {
+        const CUresult r = enc(&v.tmap[k], dt, 4, v.f[k], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(h, LBM_ERR_CUDA, "tensor map of level %d buffer %d (driver error %d)", l, k, (int)r);
+    }
+    return LBM_OK;
+}
+
 int upload_all(lbm_h h)
 {
     bool ok = true;
@@ -693,6 +778,11 @@ int upload_all(lbm_h h)
                 slot_tag[(size_t)(x + v.px * yz)] = v.tag[(size_t)idx];
             }
             v.d_tag = upload(h, slot_tag, &ok);
+        }
+        if (h->D == 3) {
+            int rc = make_tensor_maps(h, l);
+            if (rc == LBM_OK) rc = plan_chunks(h, l);
+            if (rc != LBM_OK) return rc;
         }
         const size_t ni = std::max(1, v.nif), as = arith_size(h->d.storage);
         v.if_pop = dev_alloc(h, ni * Q * as);
@@ -829,8 +919,9 @@ struct Sched {
         if constexpr (Lat<Q>::D == 2)
             launch_bulk2d<Q, S>(h, l, v.tile_cfg, src, dst, tau, om, sig, sps);
         else
-            k_bulk3d<Q, S, T3X, T3Y, T3Z><<<nt, T3X * T3Y, 0, h->stream>>>(level_dev(h, l), (const S *)src, (S *)dst,
-                                                                          tau, om, sig, sps);
+            k_bulk3d<Q, S, T3X, T3Y><<<nt, T3X * T3Y, Stage3<Q, S, T3X, T3Y>::smem_bytes, h->stream>>>(
+                v.tmap[src == v.f[0] ? 0 : 1], level_dev(h, l), (const S *)src, (S *)dst, tau, om, sig, sps, v.zc,
+                h->d_status, kWaitLimitNs);
         h->launch_counter++;
         if (h->timing) {
             cudaEventRecord(h->ev_pool[ev + 1], h->stream);
@@ -1761,14 +1852,13 @@ int lbm_set_tile_config(lbm_h h, int level, int cfg)
 {
     if (!check_level(h, level)) return LBM_ERR_ARG;
     if (cfg < 0 || cfg >= LBM_TILE_CONFIGS) return fail(h, LBM_ERR_ARG, "tile configuration %d out of range", cfg);
-    if (h->D != 2) return fail(h, LBM_ERR_ARG, "tile configurations apply to D2Q9 levels");
     if (h->lev[level].tile_cfg != cfg) {
         for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);  // graphs bake the launch shapes
         h->graphs.clear();
         h->graph_launches.clear();
     }
     h->lev[level].tile_cfg = cfg;
-    return LBM_OK;
+    return h->D == 3 ? plan_chunks(h, level) : LBM_OK;
 }
 
 int lbm_get_tile_config(lbm_h h, int level, int *cfg)
@@ -1783,7 +1873,6 @@ int lbm_autotune(lbm_h h, int reps, double *us_out)
 {
     if (!h || h->batch || !h->members.empty()) return h ? fail(h, LBM_ERR_ARG, "autotune single hierarchies") : LBM_ERR_ARG;
     if (reps < 1 || reps > 10000) return fail(h, LBM_ERR_ARG, "reps must be in [1, 10000]");
-    if (h->D != 2) return LBM_OK;  // one 3-D shape
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1797,6 +1886,7 @@ int lbm_autotune(lbm_h h, int reps, double *us_out)
         for (int c = 0; c < LBM_TILE_CONFIGS; c++) {
             const int saved = v.tile_cfg;
             v.tile_cfg = c;
+            if (h->D == 3 && plan_chunks(h, l) != LBM_OK) return LBM_ERR_CUDA;
             dispatch(h, [&](auto s) { decltype(s)::bulk(h, l, src, dst); });  // warm-up
             CK(cudaEventRecord(e0, h->stream));
             for (int r = 0; r < reps; r++) dispatch(h, [&](auto s) { decltype(s)::bulk(h, l, src, dst); });
@@ -1805,6 +1895,7 @@ int lbm_autotune(lbm_h h, int reps, double *us_out)
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, e0, e1));
             v.tile_cfg = saved;
+            if (h->D == 3 && plan_chunks(h, l) != LBM_OK) return LBM_ERR_CUDA;
             const double us = 1e3 * ms / reps;
             if (us_out) us_out[l * LBM_TILE_CONFIGS + c] = us;
             if (us < best) {

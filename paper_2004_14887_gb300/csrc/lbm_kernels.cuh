@@ -1,6 +1,8 @@
 // Kernels of the GB300 direct-coupling multi-level lattice Boltzmann library.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap
+
 #include "lbm_device.cuh"
 
 namespace lbmg {
@@ -787,73 +789,122 @@ __device__ __forceinline__ int plane_class(const LevelDev &Lv, int X0, int Y0, i
     return fast ? LOAD_FAST : LOAD_GENERAL;
 }
 
-// populations (pull) and tag of the node at box coordinates (x, y, z) of a general plane:
-// periodic positions wrap; interface nodes read the table; holes and positions off a
-// non-periodic box give tag TAG_HOLE
-template <int Q, typename S>
-__device__ __forceinline__ int general_pull(const LevelDev &Lv, const S *__restrict__ fsrc, int x, int y, int z,
-                                            typename St<S>::R (&f)[Q])
+__device__ __forceinline__ unsigned long long globaltimer_ns()
 {
-    using L = Lat<Q>;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ------------------------------------------------------------------ bulk tensor copies
+// The tensor map of a 3-D population buffer is 4-D: x (n[0], contiguous), y (stride
+// px), z (stride px n[1]) and the population index (stride pitch).  One copy moves the
+// box of one population over TX+2XA x TY+4 nodes of one plane into shared memory and
+// signals an mbarrier with its byte count.
+namespace tma {
+__device__ __forceinline__ unsigned saddr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// wait for the phase with the given parity, at most limit_ns; false on time-out
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, unsigned long long limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    return true;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// element copy global -> shared without the register file (4 or 8 bytes; zero-fill when !ok)
+template <int B>
+__device__ __forceinline__ void cp_async(void *dst, const void *src, bool ok)
+{
+    static_assert(B == 4 || B == 8, "cp.async element size");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(saddr(dst)), "l"(src), "n"(B), "r"(ok ? B : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void load4d(void *dst, const CUtensorMap *map, unsigned long long *bar, int c0, int c1,
+                                       int c2, int c3)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+        "[%2];" ::"r"(saddr(dst)),
+        "l"(map), "r"(saddr(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+}  // namespace tma
+
+// shapes of the 3-D staged kernel for storage S and a TX x TY column
+template <int Q, typename S, int TX, int TY>
+struct Stage3 {
     using R = typename St<S>::R;
-    const LevelGeo &g = Lv.g;
-    const bool ok = wrap_coord(x, g.n[0], g.per[0]) && wrap_coord(y, g.n[1], g.per[1]) && wrap_coord(z, g.n[2], g.per[2]);
-    const int tag = ok ? Lv.tag[box_index(g, x, y, z)] : TAG_HOLE;
-    const R *pop = (const R *)Lv.if_pop;
-    static_for<Q>([&](auto ic) {
-        constexpr int i = decltype(ic)::value;
-        // bulk sources are nodes: a one-step wrap on periodic axes is all they need
-        int sx = x - L::c(i, 0), sy = y - L::c(i, 1), sz = z - L::c(i, 2);
-        sx += (sx < 0) ? g.n[0] : ((sx >= g.n[0]) ? -g.n[0] : 0);
-        sy += (sy < 0) ? g.n[1] : ((sy >= g.n[1]) ? -g.n[1] : 0);
-        sz += (sz < 0) ? g.n[2] : ((sz >= g.n[2]) ? -g.n[2] : 0);
-        f[i] = tag == TAG_BULK ? St<S>::ld(fsrc + (long long)i * g.pitch, box_index(g, sx, sy, sz), L::w(i))
-                               : (tag >= 0 ? pop[(long long)i * Lv.nif + tag] : R(0));
-    });
-    return tag;
-}
+    static constexpr int XA = 16 / (int)sizeof(S);   // x reach of the box below X0 (one 16-byte step)
+    static constexpr int BW = TX + 2 * XA;           // box: x in [X0-XA, X0+TX+XA), y in [Y0-2, Y0+TY+2)
+    static constexpr int BH = TY + 4;
+    static constexpr int BOX = BW * BH;               // elements of one population's box
+    static constexpr int HX = TX + 2, HY = TY + 2, HP = HX * HY;  // macro tile with its one-node halo
+    static constexpr int NRING = 4;                  // macro planes p-2 .. p+1 (one barrier per plane)
+    static constexpr size_t stage_bytes = (size_t)Q * BOX * sizeof(S);
+    static constexpr size_t ring_bytes = (size_t)NRING * 4 * HP * sizeof(R);
+    static constexpr size_t smem_bytes = 128 + 2 * stage_bytes + ring_bytes + 16;  // +128: alignment of the base
+    static_assert((BOX * sizeof(S)) % 128 == 0, "population boxes stay 128-byte aligned");
+    static_assert(BW <= 256 && BH <= 256, "tensor box limits");
+};
 
-template <int Q, typename R>
-__device__ __forceinline__ void tag_macros(const LevelDev &Lv, int tag, const R (&f)[Q], R &rho, R *u)
-{
-    constexpr int D = Lat<Q>::D;
-    rho = R(1);
-    u[0] = u[1] = u[2] = R(0);
-    if (tag == TAG_BULK) {
-        reg_moments<Q, R>(f, rho, u);
-    } else if (tag >= 0) {
-        const R *mac = (const R *)Lv.if_mac;
-        rho = mac[tag];
-#pragma unroll
-        for (int a = 0; a < D; a++) u[a] = mac[(long long)(1 + a) * Lv.nif + tag];
-    }
-}
-
-// 3-D z-marching bulk kernel: one CTA per TX x TY column of nodes and chunk of ZC
-// planes.  The CTA keeps the macros of planes z-1, z, z+1 (tile + one-node x-y halo)
-// in a 3-plane shared ring and the post-stream populations of its own nodes of plane z
-// in registers; each step pulls plane z+1 (own nodes and the 2(TX+TY)+4 halo nodes,
-// one per thread), then collides plane z.  The z halo is reused, so a node is pulled
-// 1 + (halo share) times instead of the 3-D tile's (TX+2)(TY+2)(TZ+2)/(TX TY TZ).
-template <int Q, typename S, int TX, int TY, int ZC>
-__global__ void __launch_bounds__(TX *TY) k_bulk3d(LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
-                                                    typename St<S>::R tau, typename St<S>::R om,
-                                                    typename St<S>::R sigma, typename St<S>::R spsi)
+// 3-D z-marching bulk kernel with staged planes.  One CTA per TX x TY column of nodes
+// and chunk of planes [zb, ze).  For each plane p the populations that stream into it
+// (population i from plane p - c_iz, over the column grown by XA nodes in x and 2 in
+// y) arrive in a shared-memory stage by bulk tensor copies (or, for a column that
+// meets a periodic seam in x or y, by plain loads with wrapped coordinates), one plane
+// ahead of the plane being used, in a ring of two stages with an mbarrier each.  From
+// a stage every thread pulls its node's populations (kept in registers for the next
+// step) and the macros of its node and of at most one halo node (written to a 4-plane
+// macro ring); the node of the plane below then collides with centred differences
+// taken from the ring.  Waits are bounded: on time-out the kernel sets ST_TIMEOUT,
+// waits (bounded) for its copies in flight and returns.
+template <int Q, typename S, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
+    k_bulk3d(const __grid_constant__ CUtensorMap tmap, LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
+             typename St<S>::R tau, typename St<S>::R om, typename St<S>::R sigma, typename St<S>::R spsi, int zc,
+             int *status, unsigned long long limit_ns)
 {
     using L = Lat<Q>;
+    using G = Stage3<Q, S, TX, TY>;
     using R = typename St<S>::R;
     constexpr int D = 3;
     static_assert(L::D == 3, "3-D kernel");
-    constexpr int HX = TX + 2, HY = TY + 2, HP = HX * HY;
-    constexpr int NT = TX * TY;
+    constexpr int XA = G::XA, BW = G::BW, BOX = G::BOX, HX = G::HX, HP = G::HP, NT = TX * TY;
     constexpr int NB = 2 * HX + 2 * TY;
-    static_assert(NB <= NT, "one halo column per thread at most");
-    __shared__ R s_rho[3][HP];
-    __shared__ R s_u[3][3][HP];
+    static_assert(NB <= NT, "one halo node per thread at most");
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = smem_raw + ((128u - (tma::saddr(smem_raw) & 127u)) & 127u);  // 128-byte aligned stages
+    auto stage = [&](int s) { return (S *)(base + (size_t)s * G::stage_bytes); };
+    R *s_rho = (R *)(base + 2 * G::stage_bytes);  // [NRING][HP]
+    R *s_u = s_rho + G::NRING * HP;               // [NRING][3][HP]
+    unsigned long long *bar = (unsigned long long *)(base + 2 * G::stage_bytes + G::ring_bytes);
 
     const LevelGeo &g = Lv.g;
     const int X0 = blockIdx.x * TX, Y0 = blockIdx.y * TY;
-    const int zb = blockIdx.z * ZC, ze = min(zb + ZC, g.n[2]);
+    const int zb = blockIdx.z * zc, ze = min(zb + zc, g.n[2]);
+    if (zb >= ze) return;
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
     const int x = X0 + tx, y = Y0 + ty;
@@ -866,7 +917,7 @@ __global__ void __launch_bounds__(TX *TY) k_bulk3d(LevelDev Lv, const S *__restr
             hy = 0;
         } else if (tid < 2 * HX) {
             hx = tid - HX;
-            hy = HY - 1;
+            hy = TY + 1;
         } else {
             const int b = tid - 2 * HX;
             hy = 1 + (b >> 1);
@@ -874,63 +925,202 @@ __global__ void __launch_bounds__(TX *TY) k_bulk3d(LevelDev Lv, const S *__restr
         }
         hb = hx + HX * hy;
     }
-    const int qx = X0 + hx - 1, qy = Y0 + hy - 1;
+    // own node and halo node in box coordinates (bx, by) of a stage
+    const int own_b = (ty + 2) * BW + (tx + XA);
+    const int halo_b = (hy + 1) * BW + (hx - 1 + XA);
     const int n01 = g.px * g.n[1];
+    // a column whose stage would cross a periodic seam in x or y is filled by plain loads
+    const bool seam = (g.per[0] && (X0 - 2 < 0 || X0 + TX + 1 > g.n[0] - 1)) ||
+                      (g.per[1] && (Y0 - 2 < 0 || Y0 + TY + 1 > g.n[1] - 1));
 
-    // pull plane p into (f, tag) for the own node and the macros of own and halo nodes
-    // into ring slot p mod 3
-    auto load_plane = [&](int p, R (&f)[Q], int &tag) {
-        const int cls = plane_class(Lv, X0, Y0, TX, TY, p);
-        R fh[Q];
-        int htag = TAG_HOLE;
-        tag = TAG_HOLE;
-        if (cls == LOAD_FAST) {
-            tag = TAG_BULK;
-            htag = hb >= 0 ? TAG_BULK : TAG_HOLE;
-            const int idx = x + g.px * y + n01 * p, hidx = qx + g.px * qy + n01 * p;
-            static_for<Q>([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                const int off = L::c(i, 0) + g.px * L::c(i, 1) + n01 * L::c(i, 2);
-                f[i] = St<S>::ld(fsrc + (long long)i * g.pitch, idx - off, L::w(i));
-            });
-            if (hb >= 0) {
+    // seam columns: the box elements a thread copies are the same in every plane;
+    // their wrapped x-y slot offsets (-1: off a non-periodic box) are fixed here
+    constexpr int NJ = (BOX + NT - 1) / NT;
+    int xy_off[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; j++) {
+        const int e = tid + j * NT;
+        int sx = X0 - XA + e % BW, sy = Y0 - 2 + e / BW;
+        const bool ok = e < BOX && wrap_coord(sx, g.n[0], g.per[0]) && wrap_coord(sy, g.n[1], g.per[1]);
+        xy_off[j] = ok ? sx + g.px * sy : -1;
+    }
+    if (tid == 0) {
+        tma::mbar_init(&bar[0], 1);
+        tma::mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    const int K = ze - zb + 2;  // planes zb-1 .. ze: macros of all, collisions of zb .. ze-1
+    // plane k needs a stage when it exists and is not a hole plane of this column
+    auto plane_of = [&](int k) { return zb - 1 + k; };
+    auto needed = [&](int k) {
+        const int p = plane_of(k);
+        if (!g.per[2] && (p < 0 || p >= g.n[2])) return false;
+        return plane_class(Lv, X0, Y0, TX, TY, p) != LOAD_HOLE;
+    };
+    unsigned phase = 0u, pending = 0u;  // per stage: parity of the next wait, copy in flight
+    auto issue = [&](int k) {
+        if (!needed(k)) return;
+        const int s = k & 1, p = plane_of(k);
+        S *dst = stage(s);
+        if (!seam) {
+            if (tid == 0) {
+                tma::fence_proxy_async();
+                tma::mbar_expect_tx(&bar[s], (unsigned)G::stage_bytes);
                 static_for<Q>([&](auto ic) {
                     constexpr int i = decltype(ic)::value;
-                    const int off = L::c(i, 0) + g.px * L::c(i, 1) + n01 * L::c(i, 2);
-                    fh[i] = St<S>::ld(fsrc + (long long)i * g.pitch, hidx - off, L::w(i));
+                    int zq = p - L::c(i, 2);
+                    if (g.per[2]) zq = zq < 0 ? zq + g.n[2] : (zq >= g.n[2] ? zq - g.n[2] : zq);
+                    tma::load4d(dst + i * BOX, &tmap, &bar[s], X0 - XA, Y0 - 2, zq, i);
                 });
             }
-        } else if (cls == LOAD_GENERAL) {
-            tag = general_pull<Q, S>(Lv, fsrc, x, y, p, f);
-            if (hb >= 0) htag = general_pull<Q, S>(Lv, fsrc, qx, qy, p, fh);
-        }
-        const int slot = ((p % 3) + 3) % 3;  // p may be -1 (periodic z)
-        R r, u[3];
-        tag_macros<Q, R>(Lv, tag, f, r, u);
-        s_rho[slot][hs] = r;
+            pending |= 1u << s;
+        } else {
+            // plain copies with wrapped coordinates (asynchronous for 4- and 8-byte types;
+            // completed before the barrier that precedes the stage's use)
+            int zo[3];  // slot offset of planes p+1, p, p-1 (c_z = -1, 0, 1); -1 off the box
 #pragma unroll
-        for (int a = 0; a < D; a++) s_u[slot][a][hs] = u[a];
-        if (hb >= 0) {
-            tag_macros<Q, R>(Lv, htag, fh, r, u);
-            s_rho[slot][hb] = r;
+            for (int c = 0; c < 3; c++) {
+                int sz = p + 1 - c;
+                zo[c] = wrap_coord(sz, g.n[2], g.per[2]) ? n01 * sz : -1;
+            }
+            static_for<Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                const S *src = fsrc + (long long)i * g.pitch;
+                const int z0 = zo[L::c(i, 2) + 1];
 #pragma unroll
-            for (int a = 0; a < D; a++) s_u[slot][a][hb] = u[a];
+                for (int j = 0; j < NJ; j++) {
+                    const int e = tid + j * NT;
+                    if (e >= BOX) break;
+                    const bool ok = xy_off[j] >= 0 && z0 >= 0;
+                    if constexpr (sizeof(S) >= 4)
+                        tma::cp_async<(int)sizeof(S)>(dst + i * BOX + e, ok ? src + xy_off[j] + z0 : src, ok);
+                    else
+                        dst[i * BOX + e] = ok ? src[xy_off[j] + z0] : S();
+                }
+            });
+            if constexpr (sizeof(S) >= 4) tma::cp_async_commit();
         }
-        if (!in_xy) tag = TAG_HOLE;  // a position past a periodic seam only feeds the halo
     };
 
+    // tags of the own and halo node of plane k (general planes only)
+    auto tags_of = [&](int k, int &t_own, int &t_halo) {
+        const int p = plane_of(k);
+        int ox = x, oy = y, oz = p;
+        const bool ok = wrap_coord(ox, g.n[0], g.per[0]) && wrap_coord(oy, g.n[1], g.per[1]) &&
+                        wrap_coord(oz, g.n[2], g.per[2]);
+        t_own = ok ? Lv.tag[box_index(g, ox, oy, oz)] : TAG_HOLE;
+        t_halo = TAG_HOLE;
+        if (hb >= 0) {
+            int qx = X0 + hx - 1, qy = Y0 + hy - 1, qz = p;
+            const bool hok = wrap_coord(qx, g.n[0], g.per[0]) && wrap_coord(qy, g.n[1], g.per[1]) &&
+                             wrap_coord(qz, g.n[2], g.per[2]);
+            t_halo = hok ? Lv.tag[box_index(g, qx, qy, qz)] : TAG_HOLE;
+        }
+    };
+
+    auto class_of = [&](int k) { return needed(k) ? plane_class(Lv, X0, Y0, TX, TY, plane_of(k)) : LOAD_HOLE; };
+
     R fc[Q], fn[Q];
-    int tc, tn;
-    if (zb >= ze) return;
-    // prologue: planes zb-1 (macros only) and zb (kept in registers); on a
-    // non-periodic z axis plane -1 does not exist and plane 0 is never bulk
-    load_plane(zb - 1 >= 0 || g.per[2] ? zb - 1 : zb, fn, tn);
-    load_plane(zb, fc, tc);
-    for (int z = zb; z < ze; z++) {
-        load_plane(z + 1 < g.n[2] || g.per[2] ? z + 1 : z, fn, tn);
+    int tc = TAG_HOLE, tn = TAG_HOLE;
+    int nt_own = TAG_HOLE, nt_halo = TAG_HOLE;  // tags of the next general plane (loaded one plane ahead)
+    issue(0);
+    issue(1);
+    if (seam) {  // stages filled by plain copies
+        if constexpr (sizeof(S) >= 4) tma::cp_async_wait_all();
         __syncthreads();
-        if (tc != TAG_HOLE) {
-            const int sm = (z + 2) % 3, s0 = z % 3, sp = (z + 1) % 3;  // planes z-1, z, z+1
+    }
+    int ncls = class_of(0);
+    if (ncls == LOAD_GENERAL) tags_of(0, nt_own, nt_halo);
+    for (int k = 0; k < K; k++) {
+        const int p = plane_of(k);
+        const int s = k & 1;
+        const int cls = ncls;
+        const int t_own = cls == LOAD_FAST ? TAG_BULK : nt_own, t_halo = cls == LOAD_FAST ? TAG_BULK : nt_halo;
+        if (k + 1 < K) {
+            ncls = class_of(k + 1);
+            if (ncls == LOAD_GENERAL) tags_of(k + 1, nt_own, nt_halo);
+        }
+        bool ok = true;
+        if (cls != LOAD_HOLE && !seam) {
+            ok = tma::mbar_wait(&bar[s], (phase >> s) & 1u, limit_ns);
+            phase ^= 1u << s;
+            if (ok) pending &= ~(1u << s);
+        }
+        // pull plane p from the stage: own node (kept) and halo node (macros only)
+        const int slot = p & (G::NRING - 1);
+        R r = R(1), u[3] = {R(0), R(0), R(0)};
+        tn = TAG_HOLE;
+        if (cls != LOAD_HOLE && ok) {
+            const S *st = stage(s);
+            tn = t_own;
+            if (tn == TAG_BULK) {
+                static_for<Q>([&](auto ic) {
+                    constexpr int i = decltype(ic)::value;
+                    fn[i] = St<S>::ld(st, i * BOX + own_b - L::c(i, 1) * BW - L::c(i, 0), L::w(i));
+                });
+                reg_moments<Q, R>(fn, r, u);
+            } else if (tn >= 0) {
+                const R *pop = (const R *)Lv.if_pop, *mac = (const R *)Lv.if_mac;
+#pragma unroll
+                for (int i = 0; i < Q; i++) fn[i] = pop[(long long)i * Lv.nif + tn];
+                r = mac[tn];
+#pragma unroll
+                for (int a = 0; a < D; a++) u[a] = mac[(long long)(1 + a) * Lv.nif + tn];
+            }
+        }
+        s_rho[slot * HP + hs] = r;
+#pragma unroll
+        for (int a = 0; a < D; a++) s_u[(slot * 3 + a) * HP + hs] = u[a];
+        if (hb >= 0) {
+            R hr = R(1), hu[3] = {R(0), R(0), R(0)};
+            if (cls != LOAD_HOLE && ok) {
+                if (t_halo == TAG_BULK) {
+                    const S *st = stage(s);
+                    R m0 = R(0), m1 = R(0), m2 = R(0), m3 = R(0);
+                    static_for<Q>([&](auto ic) {
+                        constexpr int i = decltype(ic)::value;
+                        const R v = St<S>::ld(st, i * BOX + halo_b - L::c(i, 1) * BW - L::c(i, 0), L::w(i));
+                        m0 += v;
+                        if constexpr (L::c(i, 0) > 0) m1 += v;
+                        else if constexpr (L::c(i, 0) < 0) m1 -= v;
+                        if constexpr (L::c(i, 1) > 0) m2 += v;
+                        else if constexpr (L::c(i, 1) < 0) m2 -= v;
+                        if constexpr (L::c(i, 2) > 0) m3 += v;
+                        else if constexpr (L::c(i, 2) < 0) m3 -= v;
+                    });
+                    const R ir = recip(m0);
+                    hr = m0;
+                    hu[0] = m1 * ir;
+                    hu[1] = m2 * ir;
+                    hu[2] = m3 * ir;
+                } else if (t_halo >= 0) {
+                    const R *mac = (const R *)Lv.if_mac;
+                    hr = mac[t_halo];
+#pragma unroll
+                    for (int a = 0; a < D; a++) hu[a] = mac[(long long)(1 + a) * Lv.nif + t_halo];
+                }
+            }
+            s_rho[slot * HP + hb] = hr;
+#pragma unroll
+            for (int a = 0; a < D; a++) s_u[(slot * 3 + a) * HP + hb] = hu[a];
+        }
+        if (!in_xy) tn = TAG_HOLE;  // a position past a periodic seam only feeds the halo
+        if constexpr (sizeof(S) >= 4)
+            if (seam) tma::cp_async_wait_all();  // the copies of the next stage, issued one plane ago
+        if (__syncthreads_or(!ok)) {
+            // a copy did not arrive in time: report, drain what is in flight, stop
+            if (tid == 0) atomicOr(status, ST_TIMEOUT);
+            for (int q = 0; q < 2; q++)
+                if ((pending >> q) & 1u) tma::mbar_wait(&bar[q], (phase >> q) & 1u, limit_ns);
+            return;
+        }
+        if (k + 2 < K) issue(k + 2);  // into the stage just read
+        // collide plane p - 1 with the macros of planes p - 2, p - 1, p
+        if (k >= 2 && tc != TAG_HOLE) {
+            const int z = p - 1;
+            const int sm = (z - 1) & (G::NRING - 1), s0 = z & (G::NRING - 1), sp = p & (G::NRING - 1);
             R Sv[6], Cv[6];
             const int idx = x + g.px * y + n01 * z;
             if (tc == TAG_BULK) {
@@ -940,16 +1130,16 @@ __global__ void __launch_bounds__(TX *TY) k_bulk3d(LevelDev Lv, const S *__restr
                 for (int b = 0; b < 2; b++)
 #pragma unroll
                     for (int s2 = 0; s2 < 2; s2++) {
-                        nr[b][s2] = s_rho[s0][hh[b][s2]];
+                        nr[b][s2] = s_rho[s0 * HP + hh[b][s2]];
 #pragma unroll
-                        for (int a = 0; a < 3; a++) nu[b][s2][a] = s_u[s0][a][hh[b][s2]];
+                        for (int a = 0; a < 3; a++) nu[b][s2][a] = s_u[(s0 * 3 + a) * HP + hh[b][s2]];
                     }
-                nr[2][0] = s_rho[sp][hs];
-                nr[2][1] = s_rho[sm][hs];
+                nr[2][0] = s_rho[sp * HP + hs];
+                nr[2][1] = s_rho[sm * HP + hs];
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
-                    nu[2][0][a] = s_u[sp][a][hs];
-                    nu[2][1][a] = s_u[sm][a][hs];
+                    nu[2][0][a] = s_u[(sp * 3 + a) * HP + hs];
+                    nu[2][1][a] = s_u[(sm * 3 + a) * HP + hs];
                 }
                 fd_gradients<D, R>(nr, nu, R(0.5), Sv, Cv);
             } else {
@@ -957,26 +1147,27 @@ __global__ void __launch_bounds__(TX *TY) k_bulk3d(LevelDev Lv, const S *__restr
                 if (tc >= Lv.ie_base && tc < Lv.ie_base + Lv.n_ie) {
                     const int e = tc - Lv.ie_base, nst = Lv.ie_nst[e];
 #pragma unroll
-                    for (int k = 0; k < 6; k++) Sv[k] = Cv[k] = R(0);
+                    for (int q = 0; q < 6; q++) Sv[q] = Cv[q] = R(0);
                     for (int j = 0; j < nst; j++) {
                         const int tf = Lv.ie_st[e * 16 + j];
                         const R wj = (R)Lv.ie_w[e * 16 + j];
 #pragma unroll
-                        for (int k = 0; k < 6; k++) {
-                            Sv[k] += wj * tS[(long long)k * Lv.nif + tf];
-                            Cv[k] += wj * tC[(long long)k * Lv.nif + tf];
+                        for (int q = 0; q < 6; q++) {
+                            Sv[q] += wj * tS[(long long)q * Lv.nif + tf];
+                            Cv[q] += wj * tC[(long long)q * Lv.nif + tf];
                         }
                     }
                 } else {
 #pragma unroll
-                    for (int k = 0; k < 6; k++) {
-                        Sv[k] = tS[(long long)k * Lv.nif + tc];
-                        Cv[k] = tC[(long long)k * Lv.nif + tc];
+                    for (int q = 0; q < 6; q++) {
+                        Sv[q] = tS[(long long)q * Lv.nif + tc];
+                        Cv[q] = tC[(long long)q * Lv.nif + tc];
                     }
                 }
             }
-            R rho = s_rho[s0][hs], u[3] = {s_u[s0][0][hs], s_u[s0][1][hs], s_u[s0][2][hs]};
-            hrr_collide<Q, R>(fc, rho, u, Sv, Cv, tau, om, sigma, spsi);
+            R rho = s_rho[s0 * HP + hs], uc[3] = {s_u[(s0 * 3) * HP + hs], s_u[(s0 * 3 + 1) * HP + hs],
+                                                  s_u[(s0 * 3 + 2) * HP + hs]};
+            hrr_collide<Q, R>(fc, rho, uc, Sv, Cv, tau, om, sigma, spsi);
             static_for<Q>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
                 St<S>::st(fdst + (long long)i * g.pitch, idx, fc[i], L::w(i));
@@ -985,10 +1176,8 @@ __global__ void __launch_bounds__(TX *TY) k_bulk3d(LevelDev Lv, const S *__restr
 #pragma unroll
         for (int i = 0; i < Q; i++) fc[i] = fn[i];
         tc = tn;
-        __syncthreads();
     }
 }
-
 
 // ------------------------------------------------------------------ batched persistent launch
 // Many independent hierarchies with the same number of levels advance together: the
@@ -1016,13 +1205,6 @@ struct BatchDev {
     unsigned int *bar_count, *bar_gen;
     unsigned long long barrier_ns;  // a barrier wait longer than this gives up
 };
-
-__device__ __forceinline__ unsigned long long globaltimer_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 
 // Grid-wide barrier of a cooperative launch.  Thread 0 of each block arrives on a
 // counter; the last arrival resets it and bumps the generation; the others wait for
