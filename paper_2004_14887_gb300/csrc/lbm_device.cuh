@@ -90,19 +90,19 @@ template <> struct St<double> {
 };
 template <> struct St<float> {
     using R = float;
-    __device__ static __forceinline__ float ld(const float *p, long long k, double) { return p[k]; }
-    __device__ static __forceinline__ void st(float *p, long long k, float v, double) { p[k] = v; }
+    __device__ static __forceinline__ float ld(const float *p, long long k, float) { return p[k]; }
+    __device__ static __forceinline__ void st(float *p, long long k, float v, float) { p[k] = v; }
 };
 // IEEE half storing the deviation f_i - w_i from rest equilibrium, FP32 arithmetic
 template <> struct St<__half> {
     using R = float;
-    __device__ static __forceinline__ float ld(const __half *p, long long k, double w)
+    __device__ static __forceinline__ float ld(const __half *p, long long k, float w)
     {
-        return __half2float(p[k]) + (float)w;
+        return __half2float(p[k]) + w;
     }
-    __device__ static __forceinline__ void st(__half *p, long long k, float v, double w)
+    __device__ static __forceinline__ void st(__half *p, long long k, float v, float w)
     {
-        p[k] = __float2half_rn(v - (float)w);
+        p[k] = __float2half_rn(v - w);
     }
 };
 
@@ -142,7 +142,7 @@ struct LevelDev {
     int ie_base, n_ie;
     const int *ie_nst;
     const int *ie_st;
-    const double *ie_w;
+    const void *ie_w;  // [n_ie][16] stencil weights in the arithmetic type
 };
 
 // wrap (periodic) or reject a coordinate; returns false outside a non-periodic box

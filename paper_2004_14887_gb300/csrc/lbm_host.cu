@@ -813,12 +813,21 @@ int upload_all(lbm_h h)
         g.ie_kf = upload(h, I.ie_kf, &ok);
         g.ie_nst = upload(h, I.ie_nst, &ok);
         g.ie_st = upload(h, I.ie_st, &ok);
-        g.ie_w = upload(h, I.ie_w, &ok);
+        if (h->d.storage == LBM_F64) {
+            g.ie_w = upload(h, I.ie_w, &ok);
+        } else {
+            const std::vector<float> w32(I.ie_w.begin(), I.ie_w.end());  // Lagrange weights: exact in FP32
+            for (size_t k = 0; k < w32.size(); k++)
+                if ((double)w32[k] != I.ie_w[k]) return fail(h, LBM_ERR_BAD_DESC, "internal: stencil weight not exact in FP32");
+            g.ie_w = upload(h, w32, &ok);
+        }
         g.ring_c = upload(h, coords3(h->lev[l - 1], I.ring_coarse), &ok);
         g.hist_f = dev_alloc(h, (size_t)3 * Q * std::max(1, g.nTF) * arith_size(h->d.storage));
         g.hist_m = dev_alloc(h, (size_t)3 * 4 * std::max(1, g.nRing) * arith_size(h->d.storage));
         g.tfc_base = h->lev[l - 1].nTFP + h->lev[l - 1].nIE;
         g.R = I.R;
+        g.Rf = (float)I.R;
+        g.Rinv = 1.0 / I.R;
         if (!ok || !g.hist_f || !g.hist_m) return fail(h, LBM_ERR_OOM, "interface %d tables", l);
     }
     h->d_status = (int *)dev_alloc(h, 2 * sizeof(int));
@@ -929,27 +938,7 @@ struct Sched {
         }
     }
 
-    static TimeW weights(int phase, long long kp)
-    {
-        TimeW tw{};
-        tw.slot[0] = (int)((kp + 2) % 3);
-        tw.slot[1] = (int)(kp % 3);
-        tw.slot[2] = (int)((kp + 1) % 3);
-        if (phase == 1) {
-            tw.w[0] = 0.0;
-            tw.w[1] = 0.0;
-            tw.w[2] = 1.0;
-        } else if (kp == 0) {
-            tw.w[0] = 0.0;
-            tw.w[1] = 0.5;
-            tw.w[2] = 0.5;
-        } else {
-            tw.w[0] = -1.0 / 8.0;  // Eq. (TempInt)
-            tw.w[1] = 3.0 / 4.0;
-            tw.w[2] = 3.0 / 8.0;
-        }
-        return tw;
-    }
+    static TimeW weights(int phase, long long kp) { return time_weights(phase, kp); }
 
     // one step of level l (Sec. 3.5): k is the level's step index, kp its parent's
     static void level_step(lbm_h h, int l, long long k, int phase, long long kp)

@@ -25,18 +25,53 @@ struct IfaceDev {
     const unsigned int *ie_kf;
     const int *ie_nst;
     const int *ie_st;               // [nIE][16] TF indices
-    const double *ie_w;             // [nIE][16]
+    const void *ie_w;               // [nIE][16] Lagrange weights in the arithmetic type R
     const int *ring_c;              // [nRing][3] coarse-level box coordinates
     void *hist_f;                   // [3][Q][nTF] coarse post-stream populations at TF nodes (type R)
     void *hist_m;                   // [3][4][nRing] coarse post-stream macros on the ring (type R)
     int tfc_base;                   // table index of the first TF node in the coarse level's table
     double R;                       // Eq. (fneqResc): R = tau_f / (2 tau_c)
+    float Rf;                       // R in FP32
+    double Rinv;                    // 1 / R
 };
 
 struct TimeW {
     int slot[3];   // t - dt^c, t, t + dt^c
     double w[3];   // weights (Eq. TempInt, linear on the first coarse step, [0,0,1] on sync)
+    float wf[3];   // the same in FP32
+    int nz;        // bit k: w[k] != 0
 };
+
+// Eq. (TempInt) weights of the parent's history slots for a fine sub-step: phase 1
+// (synchronous) takes the parent's new state, the first coarse step interpolates
+// linearly, later ones quadratically through t - dt^c, t, t + dt^c.  kp is the
+// parent's step index; the history ring holds slot (kp + 1) % 3 as the newest.
+__host__ __device__ __forceinline__ TimeW time_weights(int phase, long long kp)
+{
+    TimeW tw{};
+    tw.slot[0] = (int)((kp + 2) % 3);
+    tw.slot[1] = (int)(kp % 3);
+    tw.slot[2] = (int)((kp + 1) % 3);
+    if (phase == 1) {
+        tw.w[0] = 0.0, tw.w[1] = 0.0, tw.w[2] = 1.0;
+        tw.wf[0] = 0.0f, tw.wf[1] = 0.0f, tw.wf[2] = 1.0f;
+        tw.nz = 4;
+    } else if (kp == 0) {
+        tw.w[0] = 0.0, tw.w[1] = 0.5, tw.w[2] = 0.5;
+        tw.wf[0] = 0.0f, tw.wf[1] = 0.5f, tw.wf[2] = 0.5f;
+        tw.nz = 6;
+    } else {
+        tw.w[0] = -1.0 / 8.0, tw.w[1] = 3.0 / 4.0, tw.w[2] = 3.0 / 8.0;
+        tw.wf[0] = -1.0f / 8.0f, tw.wf[1] = 3.0f / 4.0f, tw.wf[2] = 3.0f / 8.0f;
+        tw.nz = 7;
+    }
+    return tw;
+}
+
+// weight k of a TimeW in the arithmetic type R
+template <typename R> __device__ __forceinline__ R tw_w(const TimeW &tw, int k);
+template <> __device__ __forceinline__ double tw_w<double>(const TimeW &tw, int k) { return tw.w[k]; }
+template <> __device__ __forceinline__ float tw_w<float>(const TimeW &tw, int k) { return tw.wf[k]; }
 
 __device__ __forceinline__ int box_index(const LevelGeo &g, int x, int y, int z)
 {
@@ -88,19 +123,19 @@ __device__ __forceinline__ T seg_sum(T v)
 }
 
 // velocity and weight of a run-time population index
-template <int Q>
-__device__ __forceinline__ void lane_lattice(int i, int &cx, int &cy, int &cz, double &w)
+template <int Q, typename T>
+__device__ __forceinline__ void lane_lattice(int i, int &cx, int &cy, int &cz, T &w)
 {
     using L = Lat<Q>;
     cx = cy = cz = 0;
-    w = 0.0;
+    w = T(0);
 #pragma unroll
     for (int j = 0; j < Q; j++)
         if (i == j) {
             cx = L::c(j, 0);
             cy = L::c(j, 1);
             cz = L::c(j, 2);
-            w = L::w(j);
+            w = T(L::w(j));
         }
 }
 
@@ -134,6 +169,30 @@ __device__ __forceinline__ T feq_lane(const int *c, T w, T rho, const T *u, T *d
             d[1 + g] = w * rho * (T(3) * T(c[g]) + T(9) * cu * T(c[g]) - T(3) * u[g] + T(13.5) * dh3[g]);
     }
     return w * rho * p;
+}
+
+// Eq. (fEq_herm) of one population in FP64, for the rescalings of Eqs. (rescff) and
+// (rescfc), written with few FP64 operations (GB300 runs FP64 at 1/64 of the FP32
+// rate).  For velocities with components in {-1, 0, 1}, with cu = c.u, uu = u.u,
+// V = sum_a c_a^2 u_a^2 and W3 = sum_b c_b u_b^3, the third-order Hermite term
+// sum_{a != b} (c_a^2 - 1/3) c_b u_a^2 u_b equals cu (V - uu/3) - (2/3) W3: the inner
+// sum over a != b of (c_a^2 - 1/3) u_a^2 is V - uu/3 - (2/3) u_b^2 when c_b^2 = 1.
+template <int D>
+__device__ __forceinline__ double feq_rescale(const int *c, double w, double rho, const double *u)
+{
+    double u2[3], cu = 0.0, uu = 0.0, V = 0.0, W3 = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        u2[a] = u[a] * u[a];
+        uu += u2[a];
+        const double s = c[a] > 0 ? u[a] : (c[a] < 0 ? -u[a] : 0.0);  // c_a u_a
+        cu += s;
+        V += c[a] != 0 ? u2[a] : 0.0;
+        W3 += s * u2[a];
+    }
+    const double h3 = cu * (V - uu * (1.0 / 3.0)) - (2.0 / 3.0) * W3;
+    const double p = 1.0 + cu * (3.0 + 4.5 * cu) - 1.5 * uu + 13.5 * h3;
+    return (w * rho) * p;
 }
 
 // Newton-Raphson for F(X) = sum_i Gamma_i Phi_i (fhat_i - f0_i(X)) = 0 (Eq. system_fi)
@@ -245,11 +304,11 @@ __device__ __forceinline__ void recon_body(int bid, IfaceDev I, LevelDev F, Leve
     const bool live = seg < I.nTF;
     const int t = live ? seg : 0;
     int c[3];
-    double wd;
+    R wd;
     lane_lattice<Q>(i, c[0], c[1], c[2], wd);
     const bool pop = live && i < Q;
     // lanes beyond Q carry nothing; a segment past the last TF node solves the rest state
-    R fhat = (!live && i < Q) ? (R)wd : R(0), gam = (!live && i < Q) ? R(1) : R(0);
+    R fhat = (!live && i < Q) ? wd : R(0), gam = (!live && i < Q) ? R(1) : R(0);
     const unsigned int gcm = I.tf_gc[t];
     if (pop) {
         if ((gcm >> i) & 1u) {
@@ -257,9 +316,9 @@ __device__ __forceinline__ void recon_body(int bid, IfaceDev I, LevelDev F, Leve
             R s = R(0);
 #pragma unroll
             for (int k = 0; k < 3; k++)
-                if (tw.w[k] != 0.0) s += (R)tw.w[k] * hf[((long long)tw.slot[k] * Q + i) * I.nTF + t];
+                if ((tw.nz >> k) & 1) s += tw_w<R>(tw, k) * hf[((long long)tw.slot[k] * Q + i) * I.nTF + t];
             fhat = s;
-            gam = (R)I.R;
+            gam = sizeof(R) == 8 ? (R)I.R : (R)I.Rf;
         } else {
             if ((I.tf_kf[t] >> i) & 1u) {
                 const int s = nb_index(F.g, I.tf_f[3 * t], I.tf_f[3 * t + 1], I.tf_f[3 * t + 2], -c[0], -c[1], -c[2]);
@@ -270,7 +329,7 @@ __device__ __forceinline__ void recon_body(int bid, IfaceDev I, LevelDev F, Leve
     }
     R X[4] = {R(0), R(0), R(0), R(0)};
     const R tol = sizeof(R) == 8 ? R(1e-12) : R(2e-6);
-    const int it = newton_seg<Q, W, R>(c, i < Q ? (R)wd : R(0), fhat, gam, tol, live, X);
+    const int it = newton_seg<Q, W, R>(c, i < Q ? wd : R(0), fhat, gam, tol, live, X);
     if (!live) return;
     if (it < 0) {
         if (i == 0) atomicOr(status, ST_NEWTON);
@@ -281,12 +340,15 @@ __device__ __forceinline__ void recon_body(int bid, IfaceDev I, LevelDev F, Leve
     R *fmac = (R *)F.if_mac;
     if (i < Q) {
         // FP64 equilibrium / non-equilibrium rescaling
-        double Xd[3] = {(double)X[1], (double)X[2], (double)X[3]};
-        const double fe = feq_lane<D, double>(c, wd, (double)X[0], Xd, nullptr);
+        double w64;
+        int cc[3];
+        lane_lattice<Q>(i, cc[0], cc[1], cc[2], w64);
+        const double Xd[3] = {(double)X[1], (double)X[2], (double)X[3]};
+        const double fe = feq_rescale<D>(c, w64, (double)X[0], Xd);
         const double fh = (double)fhat;
         const double v = ((gcm >> i) & 1u) ? fe + I.R * (fh - fe) : fh;
         fpop[(long long)i * F.nif + t] = (R)v;
-        if (sync) ((R *)Cl.if_pop)[(long long)i * Cl.nif + I.tfc_base + t] = (R)(fe + (v - fe) / I.R);
+        if (sync) ((R *)Cl.if_pop)[(long long)i * Cl.nif + I.tfc_base + t] = (R)(fe + (v - fe) * I.Rinv);
     }
     if (i < 4) {
         const R xv = i <= D ? X[i] : R(0);
@@ -309,7 +371,7 @@ __device__ __forceinline__ void hist_body(int bid, IfaceDev I, LevelGeo gc, cons
     const int seg = (bid * blockDim.x + threadIdx.x) / W;
     const int i = threadIdx.x % W;
     int c[3];
-    double wd;
+    R wd;
     lane_lattice<Q>(i, c[0], c[1], c[2], wd);
     const bool is_tf = seg < I.nTF;
     const int r = seg - I.nTF;
@@ -358,7 +420,7 @@ __device__ __forceinline__ void grad_body(int bid, IfaceDev I, LevelDev F, Level
     const bool live = seg < I.nTF;
     const int t = live ? seg : 0;
     int c[3];
-    double wd;
+    R wd;
     lane_lattice<Q>(i, c[0], c[1], c[2], wd);
     const R *fmac = (const R *)F.if_mac;
     const R *hm = (const R *)I.hist_m;
@@ -391,9 +453,9 @@ __device__ __forceinline__ void grad_body(int bid, IfaceDev I, LevelDev F, Level
                 r = R(0);
 #pragma unroll
                 for (int j = 0; j < 3; j++) {
-                    if (tw.w[j] == 0.0) continue;
+                    if (!((tw.nz >> j) & 1)) continue;
                     const R *h = hm + (long long)tw.slot[j] * 4 * I.nRing;
-                    const R wj = (R)tw.w[j];
+                    const R wj = tw_w<R>(tw, j);
                     r += wj * h[ref];
 #pragma unroll
                     for (int a = 0; a < D; a++) uu[a] += wj * h[(long long)(1 + a) * I.nRing + ref];
@@ -432,7 +494,7 @@ __device__ __forceinline__ void ie_body(int bid, IfaceDev I, LevelDev F, const S
     const bool live = seg < I.nIE;
     const int e = live ? seg : 0;
     int c[3];
-    double wd;
+    R wd;
     lane_lattice<Q>(i, c[0], c[1], c[2], wd);
     const int nif = F.nif;
     const int row = I.nTF + e;  // table index of this hanging node
@@ -444,7 +506,8 @@ __device__ __forceinline__ void ie_body(int bid, IfaceDev I, LevelDev F, const S
             const int s = nb_index(F.g, I.ie_f[3 * e], I.ie_f[3 * e + 1], I.ie_f[3 * e + 2], -c[0], -c[1], -c[2]);
             if (s >= 0) v = St<S>::ld(ff, (long long)i * F.g.pitch + s, wd);
         } else {
-            for (int k = 0; k < nst; k++) v += (R)I.ie_w[e * 16 + k] * fpop[(long long)i * nif + I.ie_st[e * 16 + k]];
+            const R *iw = (const R *)I.ie_w;
+            for (int k = 0; k < nst; k++) v += iw[e * 16 + k] * fpop[(long long)i * nif + I.ie_st[e * 16 + k]];
         }
         fpop[(long long)i * nif + row] = v;
     }
@@ -571,7 +634,7 @@ __device__ __forceinline__ void collide_store(const LevelDev &Lv, typename St<S>
         }
         for (int j = 0; j < nst; j++) {
             const int tf = Lv.ie_st[e * 16 + j];
-            const R wj = (R)Lv.ie_w[e * 16 + j];
+            const R wj = ((const R *)Lv.ie_w)[e * 16 + j];
 #pragma unroll
             for (int k = 0; k < 6; k++) {
                 Sv[k] += wj * tS[(long long)k * Lv.nif + tf];
@@ -1150,7 +1213,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
                     for (int q = 0; q < 6; q++) Sv[q] = Cv[q] = R(0);
                     for (int j = 0; j < nst; j++) {
                         const int tf = Lv.ie_st[e * 16 + j];
-                        const R wj = (R)Lv.ie_w[e * 16 + j];
+                        const R wj = ((const R *)Lv.ie_w)[e * 16 + j];
 #pragma unroll
                         for (int q = 0; q < 6; q++) {
                             Sv[q] += wj * tS[(long long)q * Lv.nif + tf];
@@ -1253,27 +1316,7 @@ __device__ __forceinline__ int owner(const int *pre, int n, int t)
     return lo;
 }
 
-__device__ __forceinline__ TimeW batch_weights(int phase, long long kp)
-{
-    TimeW tw;
-    tw.slot[0] = (int)((kp + 2) % 3);
-    tw.slot[1] = (int)(kp % 3);
-    tw.slot[2] = (int)((kp + 1) % 3);
-    if (phase == 1) {
-        tw.w[0] = 0.0;
-        tw.w[1] = 0.0;
-        tw.w[2] = 1.0;
-    } else if (kp == 0) {
-        tw.w[0] = 0.0;
-        tw.w[1] = 0.5;
-        tw.w[2] = 0.5;
-    } else {
-        tw.w[0] = -1.0 / 8.0;  // Eq. (TempInt)
-        tw.w[1] = 3.0 / 4.0;
-        tw.w[2] = 3.0 / 8.0;
-    }
-    return tw;
-}
+__device__ __forceinline__ TimeW batch_weights(int phase, long long kp) { return time_weights(phase, kp); }
 
 template <int Q, typename S, int TX, int TYT, int NR>
 __global__ void __launch_bounds__(TX *TYT) k_batch(BatchDev B, const BatchPhase *__restrict__ phases, int nphases,
