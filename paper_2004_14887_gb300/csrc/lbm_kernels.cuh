@@ -973,21 +973,26 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
     const int x = X0 + tx, y = Y0 + ty;
     const bool in_xy = x < g.n[0] && y < g.n[1];
     const int hs = (tx + 1) + HX * (ty + 1);
+    // halo nodes are dealt out to every warp (node w + NW * lane of warp w), so that no
+    // warp reaches the per-plane barrier late
+    constexpr int NW = NT / 32;
+    const int hn = (tid >> 5) + NW * (tid & 31);
     int hb = -1, hx = 0, hy = 0;
-    if (tid < NB) {
-        if (tid < HX) {
-            hx = tid;
+    if (hn < NB) {
+        if (hn < HX) {
+            hx = hn;
             hy = 0;
-        } else if (tid < 2 * HX) {
-            hx = tid - HX;
+        } else if (hn < 2 * HX) {
+            hx = hn - HX;
             hy = TY + 1;
         } else {
-            const int b = tid - 2 * HX;
+            const int b = hn - 2 * HX;
             hy = 1 + (b >> 1);
             hx = (b & 1) ? HX - 1 : 0;
         }
         hb = hx + HX * hy;
     }
+    const bool issuer = tid == NT - 32;  // lane 0 of the last warp issues the tensor copies
     // own node and halo node in box coordinates (bx, by) of a stage
     const int own_b = (ty + 2) * BW + (tx + XA);
     const int halo_b = (hy + 1) * BW + (hx - 1 + XA);
@@ -1007,7 +1012,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
         const bool ok = e < BOX && wrap_coord(sx, g.n[0], g.per[0]) && wrap_coord(sy, g.n[1], g.per[1]);
         xy_off[j] = ok ? sx + g.px * sy : -1;
     }
-    if (tid == 0) {
+    if (issuer) {
         tma::mbar_init(&bar[0], 1);
         tma::mbar_init(&bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1015,20 +1020,20 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
     __syncthreads();
 
     const int K = ze - zb + 2;  // planes zb-1 .. ze: macros of all, collisions of zb .. ze-1
-    // plane k needs a stage when it exists and is not a hole plane of this column
+    // class of plane k: a plane off a non-periodic box counts as a hole plane (no stage)
     auto plane_of = [&](int k) { return zb - 1 + k; };
-    auto needed = [&](int k) {
+    auto class_of = [&](int k) {
         const int p = plane_of(k);
-        if (!g.per[2] && (p < 0 || p >= g.n[2])) return false;
-        return plane_class(Lv, X0, Y0, TX, TY, p) != LOAD_HOLE;
+        if (!g.per[2] && (p < 0 || p >= g.n[2])) return (int)LOAD_HOLE;
+        return plane_class(Lv, X0, Y0, TX, TY, p);
     };
     unsigned phase = 0u, pending = 0u;  // per stage: parity of the next wait, copy in flight
-    auto issue = [&](int k) {
-        if (!needed(k)) return;
+    auto issue = [&](int k, int cls_k) {
+        if (cls_k == LOAD_HOLE) return;
         const int s = k & 1, p = plane_of(k);
         S *dst = stage(s);
         if (!seam) {
-            if (tid == 0) {
+            if (issuer) {
                 tma::fence_proxy_async();
                 tma::mbar_expect_tx(&bar[s], (unsigned)G::stage_bytes);
                 static_for<Q>([&](auto ic) {
@@ -1083,28 +1088,23 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
         }
     };
 
-    auto class_of = [&](int k) { return needed(k) ? plane_class(Lv, X0, Y0, TX, TY, plane_of(k)) : LOAD_HOLE; };
-
     R fc[Q], fn[Q];
     int tc = TAG_HOLE, tn = TAG_HOLE;
     int nt_own = TAG_HOLE, nt_halo = TAG_HOLE;  // tags of the next general plane (loaded one plane ahead)
-    issue(0);
-    issue(1);
+    int c0 = class_of(0), c1 = class_of(1);  // classes of planes k, k + 1 (K >= 3)
+    issue(0, c0);
+    issue(1, c1);
     if (seam) {  // stages filled by plain copies
         if constexpr (sizeof(S) >= 4) tma::cp_async_wait_all();
         __syncthreads();
     }
-    int ncls = class_of(0);
-    if (ncls == LOAD_GENERAL) tags_of(0, nt_own, nt_halo);
+    if (c0 == LOAD_GENERAL) tags_of(0, nt_own, nt_halo);
     for (int k = 0; k < K; k++) {
         const int p = plane_of(k);
         const int s = k & 1;
-        const int cls = ncls;
+        const int cls = c0;
         const int t_own = cls == LOAD_FAST ? TAG_BULK : nt_own, t_halo = cls == LOAD_FAST ? TAG_BULK : nt_halo;
-        if (k + 1 < K) {
-            ncls = class_of(k + 1);
-            if (ncls == LOAD_GENERAL) tags_of(k + 1, nt_own, nt_halo);
-        }
+        if (k + 1 < K && c1 == LOAD_GENERAL) tags_of(k + 1, nt_own, nt_halo);
         bool ok = true;
         if (cls != LOAD_HOLE && !seam) {
             ok = tma::mbar_wait(&bar[s], (phase >> s) & 1u, limit_ns);
@@ -1179,7 +1179,10 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
                 if ((pending >> q) & 1u) tma::mbar_wait(&bar[q], (phase >> q) & 1u, limit_ns);
             return;
         }
-        if (k + 2 < K) issue(k + 2);  // into the stage just read
+        const int c2 = k + 2 < K ? class_of(k + 2) : (int)LOAD_HOLE;
+        if (k + 2 < K) issue(k + 2, c2);  // into the stage just read
+        c0 = c1;
+        c1 = c2;
         // collide plane p - 1 with the macros of planes p - 2, p - 1, p
         if (k >= 2 && tc != TAG_HOLE) {
             const int z = p - 1;
