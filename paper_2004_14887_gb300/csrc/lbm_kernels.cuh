@@ -663,10 +663,14 @@ __device__ __forceinline__ void collide_store(const LevelDev &Lv, typename St<S>
 // neighbours (or the supplied S, C of interface nodes) and collides.  The
 // 2(TX+TY)+4 halo nodes are shared out one per thread; all loads of a thread (its
 // nodes and its halo node) go out before any is used.
-template <int Q, typename S, int TX, int TYT, int NR>
-__device__ __forceinline__ void bulk2d_tile(const LevelDev &Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
+// NBUF = 2 keeps two sets of the shared macro arrays (buf = 0, 1): a CTA that runs
+// tiles back to back alternates them after every tile that returned true (a tile
+// that passed its barrier) and needs no barrier between tiles.  Returns false for a
+// skipped tile.
+template <int Q, typename S, int TX, int TYT, int NR, int NBUF = 1>
+__device__ __forceinline__ bool bulk2d_tile(const LevelDev &Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
                                             typename St<S>::R tau, typename St<S>::R om, typename St<S>::R sigma,
-                                            typename St<S>::R spsi, int bx, int by)
+                                            typename St<S>::R spsi, int bx, int by, int buf = 0)
 {
     using L = Lat<Q>;
     using R = typename St<S>::R;
@@ -678,13 +682,15 @@ __device__ __forceinline__ void bulk2d_tile(const LevelDev &Lv, const S *__restr
     constexpr int NT = TX * TYT;
     constexpr int NB = 2 * HX + 2 * TY;  // halo positions
     static_assert(NB <= NT, "one halo node per thread at most");
-    __shared__ R s_rho[H];
-    __shared__ R s_u[D * H];
+    __shared__ R s_rho_all[NBUF][H];
+    __shared__ R s_u_all[NBUF][D * H];
+    R *s_rho = s_rho_all[NBUF > 1 ? buf : 0];
+    R *s_u = s_u_all[NBUF > 1 ? buf : 0];
     const LevelGeo &g = Lv.g;
     const int X0 = bx * TX, Y0 = by * TY;
     const int t0[3] = {X0, Y0, 0}, T[3] = {TX, TY, 1};
     const unsigned char flag = tile_class<D>(Lv, t0, T);
-    if (flag == TILE_SKIP) return;
+    if (flag == TILE_SKIP) return false;
     const int tid = threadIdx.x;
     const int tx = tid % TX, tr = tid / TX;
     const int x = X0 + tx;
@@ -813,6 +819,7 @@ __device__ __forceinline__ void bulk2d_tile(const LevelDev &Lv, const S *__restr
         collide_store<Q, S, HX, HY, H>(Lv, f[r], rho[r], u[r], tag[r], hs, s_rho, s_u, tau, om, sigma, spsi, fdst,
                                        idx[r]);
     }
+    return true;
 }
 
 template <int Q, typename S, int TX, int TYT, int NR>
@@ -1321,12 +1328,54 @@ __device__ __forceinline__ int owner(const int *pre, int n, int t)
 
 __device__ __forceinline__ TimeW batch_weights(int phase, long long kp) { return time_weights(phase, kp); }
 
+// Phase bodies of the batched kernel as separate (not inlined) functions: each gets
+// its own register allocation instead of the union of all phases.
 template <int Q, typename S, int TX, int TYT, int NR>
-__global__ void __launch_bounds__(TX *TYT) k_batch(BatchDev B, const BatchPhase *__restrict__ phases, int nphases,
-                                                    long long k0, int nsteps)
+__device__ __forceinline__ bool batch_bulk_tile(const LevelDev &Lv, long long kl, int local, int buf)
+{
+    using R = typename St<S>::R;
+    const bool dbl = sizeof(R) == 8;
+    return bulk2d_tile<Q, S, TX, TYT, NR, 2>(Lv, (const S *)Lv.f[kl & 1], (S *)Lv.f[(kl + 1) & 1],
+                                      dbl ? (R)Lv.tau : (R)Lv.tauf, dbl ? (R)Lv.om : (R)Lv.omf,
+                                      dbl ? (R)Lv.sigma : (R)Lv.sigmaf, dbl ? (R)Lv.spsi : (R)Lv.spsif,
+                                      local % Lv.tiles[0], local / Lv.tiles[0], buf);
+}
+template <int Q, typename S>
+__device__ __noinline__ void batch_recon_hist(const BatchDev &B, int h, int l, long long kl, int local, TimeW tw)
+{
+    const int nbr = B.nb_recon[(size_t)l * B.n + h];
+    const LevelDev &F = B.lev[h * B.L + l];
+    const S *fA = (const S *)F.f[kl & 1];
+    if (local < nbr)
+        recon_body<Q, S>(local, B.ifc[h * B.L + l], F, B.lev[h * B.L + l - 1], fA, tw, (int)(kl & 1), B.status,
+                         B.max_iters);
+    else
+        hist_body<Q, S>(local - nbr, B.ifc[h * B.L + l + 1], F.g, fA, (int)((kl + 1) % 3), 0);
+}
+template <int Q, typename S>
+__device__ __noinline__ void batch_grad_ie(const BatchDev &B, int h, int l, long long kl, int local, TimeW tw)
+{
+    const int nbg = B.nb_grad[(size_t)l * B.n + h];
+    const LevelDev &F = B.lev[h * B.L + l];
+    const S *fA = (const S *)F.f[kl & 1];
+    if (local < nbg)
+        grad_body<Q, S>(local, B.ifc[h * B.L + l], F, B.lev[h * B.L + l - 1], fA, tw, (int)(kl & 1));
+    else
+        ie_body<Q, S>(local - nbg, B.ifc[h * B.L + l], F, fA);
+}
+
+// Registers: at 80 registers per thread three 256-thread CTAs share an SM (a tighter
+// bound spills inside the tile body).
+template <int Q, typename S, int TX, int TYT, int NR>
+__global__ void __launch_bounds__(TX *TYT, sizeof(S) == 8 ? 1 : 3)
+    k_batch(BatchDev B, const BatchPhase *__restrict__ phases, int nphases, long long k0, int nsteps)
 {
     using R = typename St<S>::R;
     const unsigned int nb = gridDim.x;
+    // the level view of the hierarchy whose tiles a CTA works on, copied to shared
+    // memory when the CTA moves to another hierarchy or level
+    __shared__ LevelDev s_lv;
+    static_assert(sizeof(LevelDev) % 4 == 0, "word copy");
     for (int st = 0; st < nsteps; st++) {
         const long long k = k0 + st;
         for (int pi = 0; pi < nphases; pi++) {
@@ -1335,45 +1384,33 @@ __global__ void __launch_bounds__(TX *TYT) k_batch(BatchDev B, const BatchPhase 
             const long long kl = (k << l) + ph.sub;
             if (ph.kind == PH_BULK) {
                 const int *pre = B.pre_bulk + (size_t)l * (B.n + 1);
+                int cur = -1, nbuf = 0;
                 for (int t = blockIdx.x; t < pre[B.n]; t += nb) {
                     const int h = owner(pre, B.n, t);
-                    const LevelDev &Lv = B.lev[h * B.L + l];
-                    const int local = t - pre[h];
-                    const bool dbl = sizeof(R) == 8;
-                    bulk2d_tile<Q, S, TX, TYT, NR>(Lv, (const S *)Lv.f[kl & 1], (S *)Lv.f[(kl + 1) & 1],
-                                                   dbl ? (R)Lv.tau : (R)Lv.tauf, dbl ? (R)Lv.om : (R)Lv.omf,
-                                                   dbl ? (R)Lv.sigma : (R)Lv.sigmaf, dbl ? (R)Lv.spsi : (R)Lv.spsif,
-                                                   local % Lv.tiles[0], local / Lv.tiles[0]);
-                    __syncthreads();  // the tile's shared arrays are reused by the next item
+                    if (h != cur) {
+                        __syncthreads();  // the previous view is no longer read
+                        const int *src = (const int *)&B.lev[h * B.L + l];
+                        for (int w = threadIdx.x; w < (int)(sizeof(LevelDev) / 4); w += blockDim.x)
+                            ((int *)&s_lv)[w] = src[w];
+                        __syncthreads();
+                        cur = h;
+                    }
+                    if (batch_bulk_tile<Q, S, TX, TYT, NR>(s_lv, kl, t - pre[h], nbuf))
+                        nbuf ^= 1;  // alternate shared arrays: no barrier between tiles
                 }
             } else if (ph.kind == PH_RH) {
                 const int *pre = B.pre_rh + (size_t)l * (B.n + 1);
                 const TimeW tw = l > 0 ? batch_weights((int)(kl & 1), kl >> 1) : TimeW{};
                 for (int t = blockIdx.x; t < pre[B.n]; t += nb) {
                     const int h = owner(pre, B.n, t);
-                    const int local = t - pre[h];
-                    const int nbr = B.nb_recon[(size_t)l * B.n + h];
-                    const LevelDev &F = B.lev[h * B.L + l];
-                    const S *fA = (const S *)F.f[kl & 1];
-                    if (local < nbr)
-                        recon_body<Q, S>(local, B.ifc[h * B.L + l], F, B.lev[h * B.L + l - 1], fA, tw, (int)(kl & 1),
-                                         B.status, B.max_iters);
-                    else
-                        hist_body<Q, S>(local - nbr, B.ifc[h * B.L + l + 1], F.g, fA, (int)((kl + 1) % 3), 0);
+                    batch_recon_hist<Q, S>(B, h, l, kl, t - pre[h], tw);
                 }
             } else {
                 const int *pre = B.pre_gi + (size_t)l * (B.n + 1);
                 const TimeW tw = batch_weights((int)(kl & 1), kl >> 1);
                 for (int t = blockIdx.x; t < pre[B.n]; t += nb) {
                     const int h = owner(pre, B.n, t);
-                    const int local = t - pre[h];
-                    const int nbg = B.nb_grad[(size_t)l * B.n + h];
-                    const LevelDev &F = B.lev[h * B.L + l];
-                    const S *fA = (const S *)F.f[kl & 1];
-                    if (local < nbg)
-                        grad_body<Q, S>(local, B.ifc[h * B.L + l], F, B.lev[h * B.L + l - 1], fA, tw, (int)(kl & 1));
-                    else
-                        ie_body<Q, S>(local - nbg, B.ifc[h * B.L + l], F, fA);
+                    batch_grad_ie<Q, S>(B, h, l, kl, t - pre[h], tw);
                 }
             }
             if (!ph.join_next && !grid_barrier(B.bar_count, B.bar_gen, nb, B.status, B.barrier_ns)) return;
