@@ -195,3 +195,35 @@ def test_three_level_pulse_is_stable_and_symmetric():
         m = cls != O.HOLE
         assert np.all(np.abs(r[m] - 1.0) < 2e-3)
         assert np.max(np.abs(np.where(m, r - r.T, 0.0))) < 1e-13
+
+
+def test_oracle_mirror_symmetry():
+    """A pulse at rest at the centre of a mirror-symmetric 3-level D3Q19 hierarchy
+    stays symmetric under x -> -x (a symmetry of the lattice, the collision and of
+    every interface set and stencil): pins the oracle's sets and stencils against a
+    one-sided choice, and is the reference for the full-size GPU symmetry test."""
+    d = {"lattice": 19, "coarse_n": (16, 16, 16), "boxes": [((4, 4, 4), (12, 12, 12)), ((6, 6, 6), (10, 10, 10))],
+         "nu0": 1e-5, "sigma": 0.98, "dc_variant": 2, "psi_sign": -1, "storage": "f64",
+         "init": {"kind": "pulse", "xc": 8.0, "yc": 8.0, "zc": 8.0, "Rc": 1.0, "A": 1e-3, "U": (0.0, 0.0, 0.0)}}
+    o = O.Hierarchy(d)
+    for l in range(3):
+        r, u = W.init_fields(d, l)
+        o.init(l, r, u)
+    o.advance(4)
+    for l in range(3):
+        info = o.level_info(l)
+        nx, ny, nz = info["n"]
+        r, u = o.macros(l)
+        R, U = r.reshape(nz, ny, nx), u.reshape(3, nz, ny, nx)
+        cls = o.node_class(l).reshape(nz, ny, nx)
+
+        def mirror(a):
+            f = a[..., ::-1]
+            return np.roll(f, 1, axis=-1) if info["periodic"][0] else f
+
+        assert np.array_equal(cls, mirror(cls))
+        active = cls != O.HOLE
+        assert np.max(np.abs(R - mirror(R))[active]) < 1e-14
+        assert np.max(np.abs(U[0] + mirror(U[0]))[active]) < 1e-14
+        assert np.max(np.abs(U[1] - mirror(U[1]))[active]) < 1e-14
+    assert np.max(np.abs(R - 1.0)[active]) > 1e-5  # the pulse reached the finest level's nodes
