@@ -424,46 +424,63 @@ __device__ __forceinline__ void grad_body(int bid, IfaceDev I, LevelDev F, Level
     lane_lattice<Q>(i, c[0], c[1], c[2], wd);
     const R *fmac = (const R *)F.if_mac;
     const R *hm = (const R *)I.hist_m;
-    R rho[3][2], u[3][2][3];
+    // all stencil references first, then every load of every reference, then the
+    // reductions: two rounds of dependent loads instead of two per stencil point
+    signed char kind[3][2];
+    int ref[3][2];
 #pragma unroll
     for (int b = 0; b < D; b++)
 #pragma unroll
         for (int s = 0; s < 2; s++) {
             const int k = t * 2 * D + 2 * b + s;
-            const signed char kind = I.tf_rkind[k];
-            const int ref = I.tf_ridx[k];
+            kind[b][s] = I.tf_rkind[k];
+            ref[b][s] = I.tf_ridx[k];
+        }
+    R v[3][2], rho[3][2], u[3][2][3];
+#pragma unroll
+    for (int b = 0; b < D; b++)
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+            const int kd = kind[b][s], rf = ref[b][s];
             // fine neighbour: lane i pulls its population i (zero for other kinds)
-            R v = R(0);
-            if (live && kind == RK_FINE && i < Q) {
-                const int x = ref % F.g.n[0], yz = ref / F.g.n[0];
+            v[b][s] = R(0);
+            if (live && kd == RK_FINE && i < Q) {
+                const int x = rf % F.g.n[0], yz = rf / F.g.n[0];
                 const int src = nb_index(F.g, x, yz % F.g.n[1], yz / F.g.n[1], -c[0], -c[1], -c[2]);
-                if (src >= 0) v = St<S>::ld(ff, (long long)i * F.g.pitch + src, wd);
+                if (src >= 0) v[b][s] = St<S>::ld(ff, (long long)i * F.g.pitch + src, wd);
             }
-            R r = seg_sum<W>(v), uu[3] = {R(0), R(0), R(0)};
+            rho[b][s] = R(0);
 #pragma unroll
-            for (int a = 0; a < D; a++) uu[a] = seg_sum<W>(R(c[a]) * v);
-            if (kind == RK_FINE) {
+            for (int a = 0; a < 3; a++) u[b][s][a] = R(0);
+            if (kd == RK_TF) {
+                rho[b][s] = fmac[rf];
 #pragma unroll
-                for (int a = 0; a < D; a++) uu[a] /= r;
-            } else if (kind == RK_TF) {
-                r = fmac[ref];
-#pragma unroll
-                for (int a = 0; a < D; a++) uu[a] = fmac[(long long)(1 + a) * F.nif + ref];
-            } else {
-                r = R(0);
+                for (int a = 0; a < D; a++) u[b][s][a] = fmac[(long long)(1 + a) * F.nif + rf];
+            } else if (kd != RK_FINE) {
 #pragma unroll
                 for (int j = 0; j < 3; j++) {
                     if (!((tw.nz >> j) & 1)) continue;
                     const R *h = hm + (long long)tw.slot[j] * 4 * I.nRing;
                     const R wj = tw_w<R>(tw, j);
-                    r += wj * h[ref];
+                    rho[b][s] += wj * h[rf];
 #pragma unroll
-                    for (int a = 0; a < D; a++) uu[a] += wj * h[(long long)(1 + a) * I.nRing + ref];
+                    for (int a = 0; a < D; a++) u[b][s][a] += wj * h[(long long)(1 + a) * I.nRing + rf];
                 }
             }
-            rho[b][s] = r;
+        }
 #pragma unroll
-            for (int a = 0; a < 3; a++) u[b][s][a] = a < D ? uu[a] : R(0);
+    for (int b = 0; b < D; b++)
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+            const R r = seg_sum<W>(v[b][s]);
+            R uu[3];
+#pragma unroll
+            for (int a = 0; a < D; a++) uu[a] = seg_sum<W>(R(c[a]) * v[b][s]);
+            if (kind[b][s] == RK_FINE) {
+                rho[b][s] = r;
+#pragma unroll
+                for (int a = 0; a < D; a++) u[b][s][a] = uu[a] / r;
+            }
         }
     if (!live) return;
     R Sg[6], Cg[6];
