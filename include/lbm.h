@@ -37,6 +37,9 @@ extern "C" {
 
 #define LBM_MAX_LEVELS 4
 #define LBM_TILE_CONFIGS 5
+#define LBM_IFACE_AUTO 0
+#define LBM_IFACE_NODE 1
+#define LBM_IFACE_SEGMENT 2
 
 #if defined(__GNUC__)
 #define LBM_API __attribute__((visibility("default")))
@@ -213,12 +216,27 @@ LBM_API int lbm_max_newton_iters(lbm_h h);
  * 3 = 64x4 x 2, 4 = 32x16 x 1.  lbm_autotune times reps launches of every shape on
  * every level (on the current state, which it leaves unchanged) and keeps the fastest
  * per level; us_out (optional, n_levels x LBM_TILE_CONFIGS) receives the measured
- * microseconds per launch.  A D3Q19 hierarchy has one shape (no-op).  Synchronises.
- * lbm_set_tile_config / lbm_get_tile_config set or read a level's shape directly (e.g.
- * from a cache of earlier autotune results); changing a shape drops the captured graphs. */
+ * microseconds per launch.  For a D3Q19 hierarchy the configurations are instead the
+ * z chunking of the z-marching bulk kernel: about 4, 2, 8, 1 or 16 waves of CTAs per
+ * launch (cfg 0..4).  Synchronises.  lbm_set_tile_config / lbm_get_tile_config set or
+ * read a level's configuration directly (e.g. from a cache of earlier autotune
+ * results); changing one drops the captured graphs.  Every configuration computes the
+ * same per-node arithmetic: results are bitwise identical. */
 LBM_API int lbm_autotune(lbm_h h, int reps, double *us_out);
 LBM_API int lbm_set_tile_config(lbm_h h, int level, int cfg);
 LBM_API int lbm_get_tile_config(lbm_h h, int level, int *cfg);
+
+/* Thread mapping of the interface kernels (Newton and rescalings of Eqs. (system_fi),
+ * (rescff), (rescfc); the history of Eq. (TempInt); the TF gradients of Sec. 3.3; the
+ * hanging-node interpolation of Sec. 3.2).  LBM_IFACE_NODE takes one node per thread
+ * (throughput, for large interfaces); LBM_IFACE_SEGMENT one 16- (D2Q9) or 32-lane
+ * (D3Q19) warp segment per node, one population per lane, with warp-shuffle sums
+ * (latency, for small interfaces).  Both evaluate the same formulas; their sums run
+ * in a different order, so results agree to rounding, not bitwise.  LBM_IFACE_AUTO,
+ * the default, takes NODE for launches of at least 32768 nodes.  Changing the mode
+ * drops the captured graphs.  Returns LBM_ERR_ARG for another mode, or for a batch
+ * (a batch takes NODE for every member: its phases cover all members' interfaces). */
+LBM_API int lbm_set_interface_mapping(lbm_h h, int mode);
 
 /* Kernel timing: while enabled, lbm_advance launches eagerly and brackets every
  * bulk collide-and-stream launch with CUDA events on the handle's stream.

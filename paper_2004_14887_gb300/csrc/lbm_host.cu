@@ -79,6 +79,7 @@ struct lbm_hierarchy {
     std::vector<DevBuf> bufs;
     int64_t device_bytes = 0;
     int *d_status = nullptr, *d_maxit = nullptr;
+    int if_mode = LBM_IFACE_AUTO;  // interface thread mapping (lbm_set_interface_mapping)
     double *d_partial = nullptr, *d_red = nullptr;
     int red_blocks = 0;
     long long ncoarse = 0;  // coarse steps done since init
@@ -488,6 +489,9 @@ int build_interfaces(lbm_h h)
 }
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // bounded device waits: 2 s
+// interface launches with at least this many nodes take one node per thread (enough
+// threads to fill 152 SMs); smaller ones take a W-lane segment per node
+constexpr int kNodeMin = 32768;
 constexpr int T2X = 32, T2YT = 8, T2NR = 2;  // D2Q9 tile: 32 x 8 threads, 2 rows per thread
 constexpr int T2Y = T2YT * T2NR;
 
@@ -906,6 +910,14 @@ void launch_bulk2d(lbm_h h, int l, int cfg, const void *src, void *dst, typename
     }
 }
 
+// one node per thread (true) or one W-lane segment per node for an interface launch of n nodes
+bool node_mapping(const lbm_h h, int n)
+{
+    if (h->if_mode == LBM_IFACE_NODE) return true;
+    if (h->if_mode == LBM_IFACE_SEGMENT) return false;
+    return n >= kNodeMin;
+}
+
 template <int Q, typename S>
 struct Sched {
     static void bulk(lbm_h h, int l, const void *src, void *dst)
@@ -946,8 +958,10 @@ struct Sched {
         Level &v = h->lev[l];
         const void *fA = v.f[k & 1];
         void *fB = v.f[(k + 1) & 1];
-        // interface kernels: one 16- (D2Q9) or 32-lane (D3Q19) segment per node, 128 threads per block
-        constexpr int SEG = 128 / (Q <= 16 ? 16 : 32);
+        // interface kernels, 128 threads per block: one node per thread when a launch has
+        // at least kNodeMin nodes (throughput), else one W-lane segment per node (latency)
+        constexpr int W = Q <= 16 ? 16 : 32;
+        auto per_block = [h](int n) { return node_mapping(h, n) ? 128 : 128 / W; };
         LevelDev dv = level_dev(h, l);
         // Newton at this level's TF nodes and the history push for the child interface
         // are independent: one launch
@@ -958,11 +972,18 @@ struct Sched {
         if (recon || hist) {
             const IfaceDev Ir = recon ? h->ifc[l].dev : IfaceDev{};
             const IfaceDev Ih = hist ? h->ifc[l + 1].dev : IfaceDev{};
-            const int nbr = recon ? (Ir.nTF + SEG - 1) / SEG : 0;
-            const int nbh = hist ? (Ih.nTF + Ih.nRing + SEG - 1) / SEG : 0;
-            k_recon_hist<Q, S><<<nbr + nbh, 128, 0, h->stream>>>(Ir, dv, l > 0 ? level_dev(h, l - 1) : dv,
-                                                                (const S *)fA, tw, phase, h->d_status, h->d_maxit, nbr,
-                                                                Ih, dv.g, (const S *)fA, (int)((k + 1) % 3));
+            const int nr = recon ? Ir.nTF : 0, nh = hist ? Ih.nTF + Ih.nRing : 0;
+            const int per = per_block(nr + nh);
+            const int nbr = (nr + per - 1) / per, nbh = (nh + per - 1) / per;
+            const LevelDev dc = l > 0 ? level_dev(h, l - 1) : dv;
+            if (per == 128)
+                k_recon_hist<Q, S, true><<<nbr + nbh, 128, 0, h->stream>>>(Ir, dv, dc, (const S *)fA, tw, phase,
+                                                                           h->d_status, h->d_maxit, nbr, Ih, dv.g,
+                                                                           (const S *)fA, (int)((k + 1) % 3));
+            else
+                k_recon_hist<Q, S, false><<<nbr + nbh, 128, 0, h->stream>>>(Ir, dv, dc, (const S *)fA, tw, phase,
+                                                                            h->d_status, h->d_maxit, nbr, Ih, dv.g,
+                                                                            (const S *)fA, (int)((k + 1) % 3));
             h->launch_counter++;
         }
         if (l + 1 < h->nl) {
@@ -971,10 +992,15 @@ struct Sched {
         }
         if (l > 0) {
             const IfaceDev &I = h->ifc[l].dev;
-            const int nbg = (I.nTF + SEG - 1) / SEG, nbi = (I.nIE + SEG - 1) / SEG;
+            const int per = per_block(I.nTF + I.nIE);
+            const int nbg = (I.nTF + per - 1) / per, nbi = (I.nIE + per - 1) / per;
             if (nbg + nbi > 0) {
-                k_grad_ie<Q, S><<<nbg + nbi, 128, 0, h->stream>>>(I, dv, level_dev(h, l - 1), (const S *)fA, tw, phase,
-                                                                  nbg);
+                if (per == 128)
+                    k_grad_ie<Q, S, true><<<nbg + nbi, 128, 0, h->stream>>>(I, dv, level_dev(h, l - 1), (const S *)fA,
+                                                                            tw, phase, nbg);
+                else
+                    k_grad_ie<Q, S, false><<<nbg + nbi, 128, 0, h->stream>>>(I, dv, level_dev(h, l - 1), (const S *)fA,
+                                                                             tw, phase, nbg);
                 h->launch_counter++;
             }
         }
@@ -993,7 +1019,7 @@ struct Sched {
         if (l + 1 < h->nl) {
             const IfaceDev &I = h->ifc[l + 1].dev;
             const int n = I.nTF + I.nRing;
-            constexpr int SEG = 128 / (Q <= 16 ? 16 : 32);
+            constexpr int SEG = 128;  // nodes per block
             if (n > 0) k_hist<Q, S><<<(n + SEG - 1) / SEG, 128, 0, h->stream>>>(I, dv.g, (const S *)v.f[0], 0, 1);
         }
         return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
@@ -1452,7 +1478,7 @@ extern "C" int lbm_reduce_static(lbm_h h, int level, double out[4])
 // ================================================================== batches
 namespace {
 constexpr int kBatchThreads = T2X * T2YT;                        // 256
-constexpr int kBatchSeg = kBatchThreads / 16;                    // D2Q9 segments per block
+constexpr int kBatchSeg = kBatchThreads / 16;                     // D2Q9 16-lane segments per work item
 
 void emit_phases(std::vector<BatchPhase> &v, int l, int sub, int L)
 {
@@ -1472,7 +1498,8 @@ int build_batch(lbm_h b)
     std::vector<LevelDev> lev((size_t)n * L);
     std::vector<IfaceDev> ifc((size_t)n * L);
     std::vector<int> pre_bulk((size_t)L * (n + 1), 0), pre_rh((size_t)L * (n + 1), 0), pre_gi((size_t)L * (n + 1), 0);
-    std::vector<int> nb_recon((size_t)L * n, 0), nb_grad((size_t)L * n, 0);
+    std::vector<int> nb_recon((size_t)L * n, 0), nb_grad((size_t)L * n, 0), node_rh((size_t)L * n, 0),
+        node_gi((size_t)L * n, 0);
     for (int hh = 0; hh < n; hh++) {
         lbm_h m = b->members[hh];
         for (int l = 0; l < L; l++) {
@@ -1480,12 +1507,19 @@ int build_batch(lbm_h b)
             if (l > 0) ifc[(size_t)hh * L + l] = m->ifc[l].dev;
             const Level &v = m->lev[l];
             const int tiles = v.tiles[0] * v.tiles[1];
-            const int nr = l > 0 ? (m->ifc[l].dev.nTF + kBatchSeg - 1) / kBatchSeg : 0;
-            const int nh = l + 1 < L ? (m->ifc[l + 1].dev.nTF + m->ifc[l + 1].dev.nRing + kBatchSeg - 1) / kBatchSeg : 0;
-            const int ng = l > 0 ? (m->ifc[l].dev.nTF + kBatchSeg - 1) / kBatchSeg : 0;
-            const int ni = l > 0 ? (m->ifc[l].dev.nIE + kBatchSeg - 1) / kBatchSeg : 0;
+            // one node per thread for every member: a batch phase covers the interfaces
+            // of all members together, so it has the throughput of a large interface
+            const int cr = l > 0 ? m->ifc[l].dev.nTF : 0;
+            const int ch = l + 1 < L ? m->ifc[l + 1].dev.nTF + m->ifc[l + 1].dev.nRing : 0;
+            const int cg = l > 0 ? m->ifc[l].dev.nTF : 0, ci = l > 0 ? m->ifc[l].dev.nIE : 0;
+            const bool nrh = true, ngi = true;
+            const int pr = nrh ? kBatchThreads : kBatchSeg, pg = ngi ? kBatchThreads : kBatchSeg;
+            const int nr = (cr + pr - 1) / pr, nh = (ch + pr - 1) / pr;
+            const int ng = (cg + pg - 1) / pg, ni = (ci + pg - 1) / pg;
             nb_recon[(size_t)l * n + hh] = nr;
             nb_grad[(size_t)l * n + hh] = ng;
+            node_rh[(size_t)l * n + hh] = nrh;
+            node_gi[(size_t)l * n + hh] = ngi;
             const size_t o = (size_t)l * (n + 1);
             pre_bulk[o + hh + 1] = pre_bulk[o + hh] + tiles;
             pre_rh[o + hh + 1] = pre_rh[o + hh] + nr + nh;
@@ -1504,6 +1538,8 @@ int build_batch(lbm_h b)
     B.nb_recon = upload(b, nb_recon, &ok);
     B.pre_gi = upload(b, pre_gi, &ok);
     B.nb_grad = upload(b, nb_grad, &ok);
+    B.node_rh = upload(b, node_rh, &ok);
+    B.node_gi = upload(b, node_gi, &ok);
     std::vector<BatchPhase> ph;
     emit_phases(ph, 0, 0, L);
     b->d_phases = upload(b, ph, &ok);
@@ -1848,6 +1884,22 @@ int lbm_set_tile_config(lbm_h h, int level, int cfg)
     }
     h->lev[level].tile_cfg = cfg;
     return h->D == 3 ? plan_chunks(h, level) : LBM_OK;
+}
+
+int lbm_set_interface_mapping(lbm_h h, int mode)
+{
+    if (!h) return LBM_ERR_ARG;
+    if (h->batch || !h->members.empty())
+        return fail(h, LBM_ERR_ARG, "the interface mapping of a batch is fixed when it is created");
+    if (mode != LBM_IFACE_AUTO && mode != LBM_IFACE_NODE && mode != LBM_IFACE_SEGMENT)
+        return fail(h, LBM_ERR_ARG, "interface mapping %d is not AUTO, NODE or SEGMENT", mode);
+    if (h->if_mode != mode) {
+        for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);  // graphs bake the launch shapes
+        h->graphs.clear();
+        h->graph_launches.clear();
+    }
+    h->if_mode = mode;
+    return LBM_OK;
 }
 
 int lbm_get_tile_config(lbm_h h, int level, int *cfg)

@@ -112,6 +112,11 @@ __device__ __forceinline__ void pulled_moments(const LevelGeo &g, const S *__res
     for (int a = 0; a < 3; a++) u[a] = a < D ? m[a] / r : R(0);
 }
 
+// ------------------------------------------------------------------ interface nodes, W-lane segments
+// Small interfaces: one 16- (D2Q9) or 32-lane (D3Q19) segment per node, one population
+// per lane, warp-shuffle sums: many threads per node keep the latency of a launch that
+// has few nodes short.  (Large interfaces use the one-node-per-thread bodies below.)
+
 // ------------------------------------------------------------------ TF reconstruction
 // segmented warp reduction over the W lanes that hold one TF node's populations
 template <int W, typename T>
@@ -291,7 +296,7 @@ __device__ int newton_seg(const int *c, T w, T fhat, T gam, T tol, bool active, 
 // the fine rebuild of gamma=c populations (Eq. rescff) and on sync sub-steps the
 // coarse rebuild of all populations (Eq. rescfc).  One W-lane segment per TF node.
 template <int Q, typename S>
-__device__ __forceinline__ void recon_body(int bid, IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict__ ff,
+__device__ __forceinline__ void recon_seg(int bid, IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict__ ff,
                                                  TimeW tw, int sync, int *status, int *max_iters)
 {
     using L = Lat<Q>;
@@ -362,7 +367,7 @@ __device__ __forceinline__ void recon_body(int bid, IfaceDev I, LevelDev F, Leve
 // macros at ring nodes, for the child level's Eq. (TempInt).  One W-lane segment
 // per node, lane i handles population i (TF segments first, then ring segments).
 template <int Q, typename S>
-__device__ __forceinline__ void hist_body(int bid, IfaceDev I, LevelGeo gc, const S *__restrict__ fc, int slot, int seed)
+__device__ __forceinline__ void hist_seg(int bid, IfaceDev I, LevelGeo gc, const S *__restrict__ fc, int slot, int seed)
 {
     using L = Lat<Q>;
     using R = typename St<S>::R;
@@ -408,7 +413,7 @@ __device__ __forceinline__ void hist_body(int bid, IfaceDev I, LevelGeo gc, cons
 // W-lane segment per TF node: the lanes pull the populations of fine neighbours in
 // parallel; every lane then holds the stencil and lanes 0..11 write S and C.
 template <int Q, typename S>
-__device__ __forceinline__ void grad_body(int bid, IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict__ ff,
+__device__ __forceinline__ void grad_seg(int bid, IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict__ ff,
                                                 TimeW tw, int sync)
 {
     using L = Lat<Q>;
@@ -500,7 +505,7 @@ __device__ __forceinline__ void grad_body(int bid, IfaceDev I, LevelDev F, Level
 // segment per hanging node, lane i completes population i.  S and C of hanging
 // nodes are interpolated with the same stencil where they are used (collide_store).
 template <int Q, typename S>
-__device__ __forceinline__ void ie_body(int bid, IfaceDev I, LevelDev F, const S *__restrict__ ff)
+__device__ __forceinline__ void ie_seg(int bid, IfaceDev I, LevelDev F, const S *__restrict__ ff)
 {
     using L = Lat<Q>;
     using R = typename St<S>::R;
@@ -536,31 +541,472 @@ __device__ __forceinline__ void ie_body(int bid, IfaceDev I, LevelDev F, const S
 }
 
 
+// ------------------------------------------------------------------ interface nodes, one per thread
+// Large interfaces take one node per thread.  A node's populations are a
+// compile-time loop (every lattice constant is a constant expression), the sums over
+// populations are register sums, and neighbouring threads hold neighbouring nodes of
+// an interface (the node lists are in box order), so the loads of one population by a
+// warp fall in few sectors.
+
+// Eq. (fEq_herm) of population I at X = (rho, u) and, if d is not null, its
+// derivatives with respect to (rho, u_1 .. u_D)
+template <int Q, int I, typename T>
+__device__ __forceinline__ T feq_pop(T rho, const T *u, T *d)
+{
+    using L = Lat<Q>;
+    constexpr int D = L::D;
+    const T w = T(L::w(I));
+    T cu = T(0), uu = T(0), h3 = T(0), dh3[3] = {T(0), T(0), T(0)};
+    static_for<D>([&](auto ac) {
+        constexpr int a = decltype(ac)::value;
+        if constexpr (L::c(I, a) > 0) cu += u[a];
+        else if constexpr (L::c(I, a) < 0) cu -= u[a];
+        uu += u[a] * u[a];
+    });
+    static_for<D>([&](auto ac) {
+        constexpr int a = decltype(ac)::value;
+        static_for<D>([&](auto bc) {
+            constexpr int b = decltype(bc)::value;
+            constexpr int ca = L::c(I, a), cb = L::c(I, b);
+            if constexpr (a != b && cb != 0) {
+                // H3_aab = (c_a^2 - cs2) c_b
+                const T k = T(((double)(ca * ca) - 1.0 / 3.0) * cb);
+                h3 += k * u[a] * u[a] * u[b];
+                if (d) {
+                    dh3[a] += k * T(2) * u[a] * u[b];
+                    dh3[b] += k * u[a] * u[a];
+                }
+            }
+        });
+    });
+    const T p = T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu + T(13.5) * h3;
+    if (d) {
+        d[0] = w * p;
+        static_for<D>([&](auto gc) {
+            constexpr int g = decltype(gc)::value;
+            constexpr T cg = T(L::c(I, g));
+            d[1 + g] = w * rho * (T(3) * cg + T(9) * cu * cg - T(3) * u[g] + T(13.5) * dh3[g]);
+        });
+    }
+    return w * rho * p;
+}
+
+// Eq. (fEq_herm) of population I in FP64, for the rescalings of Eqs. (rescff) and
+// (rescfc), with the node's velocity terms computed once (GB300 runs FP64 at 1/64 of
+// the FP32 rate).  For velocities with components in {-1, 0, 1}, with cu = c.u,
+// uu = u.u, V = sum_a c_a^2 u_a^2 and W3 = sum_b c_b u_b^3, the third-order Hermite
+// term sum_{a != b} (c_a^2 - 1/3) c_b u_a^2 u_b equals cu (V - uu/3) - (2/3) W3: the
+// inner sum over a != b of (c_a^2 - 1/3) u_a^2 is V - uu/3 - (2/3) u_b^2 when c_b^2 = 1.
+struct Feq64 {
+    double rho, u[3], u2[3], u3[3], uu;
+};
+template <int D>
+__device__ __forceinline__ Feq64 feq64_node(double rho, const double *u)
+{
+    Feq64 n;
+    n.rho = rho;
+    n.uu = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        n.u[a] = a < D ? u[a] : 0.0;
+        n.u2[a] = n.u[a] * n.u[a];
+        n.u3[a] = n.u2[a] * n.u[a];
+        if (a < D) n.uu += n.u2[a];
+    }
+    return n;
+}
+template <int Q, int I>
+__device__ __forceinline__ double feq64_pop(const Feq64 &n)
+{
+    using L = Lat<Q>;
+    constexpr int D = L::D;
+    double cu = 0.0, V = 0.0, W3 = 0.0;
+    static_for<D>([&](auto ac) {
+        constexpr int a = decltype(ac)::value;
+        if constexpr (L::c(I, a) > 0) {
+            cu += n.u[a];
+            W3 += n.u3[a];
+        } else if constexpr (L::c(I, a) < 0) {
+            cu -= n.u[a];
+            W3 -= n.u3[a];
+        }
+        if constexpr (L::c(I, a) != 0) V += n.u2[a];
+    });
+    const double h3 = cu * (V - n.uu * (1.0 / 3.0)) - (2.0 / 3.0) * W3;
+    const double p = 1.0 + cu * (3.0 + 4.5 * cu) - 1.5 * n.uu + 13.5 * h3;
+    return (L::w(I) * n.rho) * p;
+}
+
+// Newton-Raphson for F(X) = sum_i Gamma_i Phi_i (fhat_i - f0_i(X)) = 0 (Eq. system_fi)
+// at one node, Phi = (1, c_i), Gamma_i = gc where bit i of gmask is set (gamma_i = c)
+// and 1 otherwise; started from the plain moments of fhat and stopped once
+// max|dX| < tol (Eq. updated_macro).  Returns the iteration count at convergence, or
+// -1 (singular Jacobian or no convergence in 10 iterations).
+template <int Q, typename T>
+__device__ int newton_node(const T (&fhat)[Q], unsigned gmask, T gc, T tol, T (&X)[4])
+{
+    using L = Lat<Q>;
+    constexpr int D = L::D, n = D + 1;
+    T s0 = T(0), s[3] = {T(0), T(0), T(0)};
+    static_for<Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        s0 += fhat[i];
+        static_for<D>([&](auto ac) {
+            constexpr int a = decltype(ac)::value;
+            if constexpr (L::c(i, a) > 0) s[a] += fhat[i];
+            else if constexpr (L::c(i, a) < 0) s[a] -= fhat[i];
+        });
+    });
+    X[0] = s0;
+    X[3] = T(0);
+#pragma unroll
+    for (int a = 0; a < D; a++) X[1 + a] = s[a] / s0;
+    for (int it = 1; it <= 10; it++) {
+        T F[4] = {T(0), T(0), T(0), T(0)}, J[16];
+#pragma unroll
+        for (int k = 0; k < 16; k++) J[k] = T(0);
+        static_for<Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            T d[4];
+            const T fe = feq_pop<Q, i, T>(X[0], X + 1, d);
+            const T gam = ((gmask >> i) & 1u) ? gc : T(1);
+            const T r = gam * (fhat[i] - fe);
+            F[0] += r;
+#pragma unroll
+            for (int k = 0; k < n; k++) J[k] -= gam * d[k];
+            static_for<D>([&](auto ac) {
+                constexpr int a = decltype(ac)::value;
+                if constexpr (L::c(i, a) != 0) {
+                    constexpr T ca = T(L::c(i, a));
+                    F[1 + a] += ca * r;
+#pragma unroll
+                    for (int k = 0; k < n; k++) J[(1 + a) * n + k] -= ca * gam * d[k];
+                }
+            });
+        });
+        // Gaussian elimination with partial pivoting on J dX = -F
+        T b[4], dX[4];
+#pragma unroll
+        for (int r = 0; r < n; r++) b[r] = -F[r];
+#pragma unroll
+        for (int k = 0; k < n; k++) {
+            int p = k;
+#pragma unroll
+            for (int r = k + 1; r < n; r++)
+                if (fabs(J[r * n + k]) > fabs(J[p * n + k])) p = r;
+#pragma unroll
+            for (int r = k + 1; r < n; r++)
+                if (r == p) {
+#pragma unroll
+                    for (int c2 = 0; c2 < n; c2++) {
+                        const T t0 = J[k * n + c2];
+                        J[k * n + c2] = J[r * n + c2];
+                        J[r * n + c2] = t0;
+                    }
+                    const T t1 = b[k];
+                    b[k] = b[r];
+                    b[r] = t1;
+                }
+            if (J[k * n + k] == T(0)) return -1;
+#pragma unroll
+            for (int r = k + 1; r < n; r++) {
+                const T m = J[r * n + k] / J[k * n + k];
+#pragma unroll
+                for (int c2 = k; c2 < n; c2++) J[r * n + c2] -= m * J[k * n + c2];
+                b[r] -= m * b[k];
+            }
+        }
+        T mx = T(0);
+#pragma unroll
+        for (int k = n - 1; k >= 0; k--) {
+            T sum = b[k];
+#pragma unroll
+            for (int c2 = k + 1; c2 < n; c2++) sum -= J[k * n + c2] * dX[c2];
+            dX[k] = sum / J[k * n + k];
+        }
+#pragma unroll
+        for (int r = 0; r < n; r++) {
+            X[r] += dX[r];
+            mx = fmax(mx, fabs(dX[r]));
+        }
+        if (mx < tol) return it;
+    }
+    return -1;
+}
+
+// ------------------------------------------------------------------ TF reconstruction
+// Newton at TF nodes (Eq. system_fi) in the storage's arithmetic type, then, in FP64,
+// the fine rebuild of gamma=c populations (Eq. rescff) and on sync sub-steps the
+// coarse rebuild of all populations (Eq. rescfc).  One TF node per thread.
+template <int Q, typename S>
+__device__ __forceinline__ void recon_node(int bid, IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict__ ff,
+                                           TimeW tw, int sync, int *status, int *max_iters)
+{
+    using L = Lat<Q>;
+    using R = typename St<S>::R;
+    constexpr int D = L::D;
+    const int t = bid * blockDim.x + threadIdx.x;
+    if (t >= I.nTF) return;
+    const unsigned gcm = I.tf_gc[t], kfm = I.tf_kf[t];
+    const int x = I.tf_f[3 * t], y = I.tf_f[3 * t + 1], z = I.tf_f[3 * t + 2];
+    const R *hf = (const R *)I.hist_f;
+    R fhat[Q];
+    static_for<Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        R v = R(0);
+        if ((gcm >> i) & 1u) {
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                if ((tw.nz >> k) & 1) v += tw_w<R>(tw, k) * hf[((long long)tw.slot[k] * Q + i) * I.nTF + t];
+        } else if ((kfm >> i) & 1u) {
+            const int s = nb_index(F.g, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
+            if (s >= 0) v = St<S>::ld(ff, (long long)i * F.g.pitch + s, L::w(i));
+        }
+        fhat[i] = v;
+    });
+    R X[4];
+    const R tol = sizeof(R) == 8 ? R(1e-12) : R(2e-6);
+    const R gc = sizeof(R) == 8 ? (R)I.R : (R)I.Rf;
+    const int it = newton_node<Q, R>(fhat, gcm, gc, tol, X);
+    if (it < 0) {
+        atomicOr(status, ST_NEWTON);
+        return;
+    }
+    {
+        const unsigned m = __activemask();
+        const int wmax = __reduce_max_sync(m, it);
+        if ((int)(threadIdx.x & 31) == __ffs(m) - 1) atomicMax(max_iters, wmax);
+    }
+    R *fpop = (R *)F.if_pop;
+    R *cpop = (R *)Cl.if_pop;
+    const double Xd[3] = {(double)X[1], (double)X[2], (double)X[3]};
+    const Feq64 nd = feq64_node<D>((double)X[0], Xd);
+    static_for<Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        // FP64 equilibrium / non-equilibrium rescaling
+        const double fe = feq64_pop<Q, i>(nd);
+        const double fh = (double)fhat[i];
+        const double v = ((gcm >> i) & 1u) ? fe + I.R * (fh - fe) : fh;
+        fpop[(long long)i * F.nif + t] = (R)v;
+        if (sync) cpop[(long long)i * Cl.nif + I.tfc_base + t] = (R)(fe + (v - fe) * I.Rinv);
+    });
+    R *fmac = (R *)F.if_mac;
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+        const R xv = a <= D ? X[a] : R(0);
+        fmac[(long long)a * F.nif + t] = xv;
+        if (sync) ((R *)Cl.if_mac)[(long long)a * Cl.nif + I.tfc_base + t] = xv;
+    }
+}
+
+// ------------------------------------------------------------------ history push
+// post-stream coarse populations at TF nodes (coarse-known ones) and post-stream
+// macros at ring nodes, for the child level's Eq. (TempInt).  One node per thread:
+// items [0, nTF) are TF nodes, [nTF, nTF + nRing) ring nodes.  seed = 1 stores the
+// state itself (slot 0 holds the initial state).
+template <int Q, typename S>
+__device__ __forceinline__ void hist_node(int bid, IfaceDev I, LevelGeo gc, const S *__restrict__ fc, int slot, int seed)
+{
+    using L = Lat<Q>;
+    using R = typename St<S>::R;
+    constexpr int D = L::D;
+    const int item = bid * blockDim.x + threadIdx.x;
+    if (item < I.nTF) {
+        const int t = item;
+        const int x = I.tf_c[3 * t], y = I.tf_c[3 * t + 1], z = I.tf_c[3 * t + 2];
+        const unsigned kcm = I.tf_kc[t];
+        R *hf = (R *)I.hist_f;
+        static_for<Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            const int s = seed ? box_index(gc, x, y, z)
+                               : (((kcm >> i) & 1u) ? nb_index(gc, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2)) : -1);
+            hf[((long long)slot * Q + i) * I.nTF + t] = s >= 0 ? St<S>::ld(fc, (long long)i * gc.pitch + s, L::w(i)) : R(0);
+        });
+    } else if (item < I.nTF + I.nRing) {
+        const int r = item - I.nTF;
+        const int x = I.ring_c[3 * r], y = I.ring_c[3 * r + 1], z = I.ring_c[3 * r + 2];
+        R rho = R(0), m[3] = {R(0), R(0), R(0)};
+        static_for<Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            const int s = seed ? box_index(gc, x, y, z) : nb_index(gc, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
+            const R v = s >= 0 ? St<S>::ld(fc, (long long)i * gc.pitch + s, L::w(i)) : R(0);
+            rho += v;
+            static_for<D>([&](auto ac) {
+                constexpr int a = decltype(ac)::value;
+                if constexpr (L::c(i, a) > 0) m[a] += v;
+                else if constexpr (L::c(i, a) < 0) m[a] -= v;
+            });
+        });
+        R *h = (R *)I.hist_m + (long long)slot * 4 * I.nRing;
+        h[r] = rho;
+#pragma unroll
+        for (int a = 0; a < 3; a++) h[(long long)(1 + a) * I.nRing + r] = a < D ? m[a] / rho : R(0);
+    }
+}
+
+// ------------------------------------------------------------------ TF gradients
+// Sec. 3.3: centred differences over the coarse stencil (fine nodes two fine cells
+// inward, TF neighbours along the interface with their X, coarse ring nodes outward,
+// time-interpolated on async sub-steps), rescaled by 1/2 for the fine level.  One TF
+// node per thread; all stencil references are loaded before any of their data.
+template <int Q, typename S>
+__device__ __forceinline__ void grad_node(int bid, IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict__ ff,
+                                          TimeW tw, int sync)
+{
+    using L = Lat<Q>;
+    using R = typename St<S>::R;
+    constexpr int D = L::D;
+    const int t = bid * blockDim.x + threadIdx.x;
+    if (t >= I.nTF) return;
+    const R *fmac = (const R *)F.if_mac;
+    const R *hm = (const R *)I.hist_m;
+    signed char kind[3][2];
+    int ref[3][2];
+#pragma unroll
+    for (int b = 0; b < D; b++)
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+            const int k = t * 2 * D + 2 * b + s;
+            kind[b][s] = I.tf_rkind[k];
+            ref[b][s] = I.tf_ridx[k];
+        }
+    R rho[3][2], u[3][2][3];
+#pragma unroll
+    for (int b = 0; b < D; b++)
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+            const int kd = kind[b][s], rf = ref[b][s];
+            R r = R(0), m[3] = {R(0), R(0), R(0)};
+            if (kd == RK_FINE) {
+                // post-stream moments of the fine neighbour
+                const int x = rf % F.g.n[0], yz = rf / F.g.n[0];
+                const int y = yz % F.g.n[1], z = yz / F.g.n[1];
+                static_for<Q>([&](auto ic) {
+                    constexpr int i = decltype(ic)::value;
+                    const int src = nb_index(F.g, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
+                    const R v = src >= 0 ? St<S>::ld(ff, (long long)i * F.g.pitch + src, L::w(i)) : R(0);
+                    r += v;
+                    static_for<D>([&](auto ac) {
+                        constexpr int a = decltype(ac)::value;
+                        if constexpr (L::c(i, a) > 0) m[a] += v;
+                        else if constexpr (L::c(i, a) < 0) m[a] -= v;
+                    });
+                });
+#pragma unroll
+                for (int a = 0; a < D; a++) m[a] /= r;
+            } else if (kd == RK_TF) {
+                r = fmac[rf];
+#pragma unroll
+                for (int a = 0; a < D; a++) m[a] = fmac[(long long)(1 + a) * F.nif + rf];
+            } else {
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    if (!((tw.nz >> j) & 1)) continue;
+                    const R *h = hm + (long long)tw.slot[j] * 4 * I.nRing;
+                    const R wj = tw_w<R>(tw, j);
+                    r += wj * h[rf];
+#pragma unroll
+                    for (int a = 0; a < D; a++) m[a] += wj * h[(long long)(1 + a) * I.nRing + rf];
+                }
+            }
+            rho[b][s] = r;
+#pragma unroll
+            for (int a = 0; a < 3; a++) u[b][s][a] = a < D ? m[a] : R(0);
+        }
+    R Sg[6], Cg[6];
+    fd_gradients<D, R>(rho, u, R(0.5), Sg, Cg);  // coarse units: neighbours one coarse cell away
+    R *fS = (R *)F.if_S, *fC = (R *)F.if_C;
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        fS[(long long)k * F.nif + t] = R(0.5) * Sg[k];
+        fC[(long long)k * F.nif + t] = R(0.5) * Cg[k];
+        if (sync) {
+            ((R *)Cl.if_S)[(long long)k * Cl.nif + I.tfc_base + t] = Sg[k];
+            ((R *)Cl.if_C)[(long long)k * Cl.nif + I.tfc_base + t] = Cg[k];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ hanging nodes
+// 4-point 1-D Lagrange along the interface (tensor order over odd axes, one-sided
+// next to corners) of missing populations; macros are the moments.  One hanging node
+// per thread.  S and C of hanging nodes are interpolated with the same stencil where
+// they are used (collide_store).
+template <int Q, typename S>
+__device__ __forceinline__ void ie_node(int bid, IfaceDev I, LevelDev F, const S *__restrict__ ff)
+{
+    using L = Lat<Q>;
+    using R = typename St<S>::R;
+    constexpr int D = L::D;
+    const int e = bid * blockDim.x + threadIdx.x;
+    if (e >= I.nIE) return;
+    const int nif = F.nif;
+    const int row = I.nTF + e;  // table index of this hanging node
+    R *fpop = (R *)F.if_pop;
+    const R *iw = (const R *)I.ie_w;
+    const unsigned kfm = I.ie_kf[e];
+    const int nst = I.ie_nst[e];
+    const int x = I.ie_f[3 * e], y = I.ie_f[3 * e + 1], z = I.ie_f[3 * e + 2];
+    R rho = R(0), m[3] = {R(0), R(0), R(0)};
+    static_for<Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        R v = R(0);
+        if ((kfm >> i) & 1u) {
+            const int s = nb_index(F.g, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
+            if (s >= 0) v = St<S>::ld(ff, (long long)i * F.g.pitch + s, L::w(i));
+        } else {
+            for (int k = 0; k < nst; k++) v += iw[e * 16 + k] * fpop[(long long)i * nif + I.ie_st[e * 16 + k]];
+        }
+        fpop[(long long)i * nif + row] = v;
+        rho += v;
+        static_for<D>([&](auto ac) {
+            constexpr int a = decltype(ac)::value;
+            if constexpr (L::c(i, a) > 0) m[a] += v;
+            else if constexpr (L::c(i, a) < 0) m[a] -= v;
+        });
+    });
+    R *fmac = (R *)F.if_mac;
+    fmac[row] = rho;
+#pragma unroll
+    for (int a = 0; a < 3; a++) fmac[(long long)(1 + a) * nif + row] = a < D ? m[a] / rho : R(0);
+}
+
 // ------------------------------------------------------------------ fused launches
 // blocks [0, nb_a) run the first body, the rest the second: the two halves work on
 // independent data (a different interface, or TF nodes vs hanging nodes of the same
-// interface whose inputs were all written by earlier launches)
-template <int Q, typename S>
+// interface whose inputs were all written by earlier launches).  NODE selects one node
+// per thread (large interfaces) or one W-lane segment per node (small ones).
+template <int Q, typename S, bool NODE>
 __global__ void __launch_bounds__(128) k_recon_hist(IfaceDev Ir, LevelDev F, LevelDev Cl, const S *__restrict__ ff,
                                                       TimeW tw, int sync, int *status, int *max_iters, int nb_recon,
                                                       IfaceDev Ih, LevelGeo gh, const S *__restrict__ fh, int slot)
 {
-    if ((int)blockIdx.x < nb_recon) recon_body<Q, S>(blockIdx.x, Ir, F, Cl, ff, tw, sync, status, max_iters);
-    else hist_body<Q, S>(blockIdx.x - nb_recon, Ih, gh, fh, slot, 0);
+    if ((int)blockIdx.x < nb_recon) {
+        if constexpr (NODE) recon_node<Q, S>(blockIdx.x, Ir, F, Cl, ff, tw, sync, status, max_iters);
+        else recon_seg<Q, S>(blockIdx.x, Ir, F, Cl, ff, tw, sync, status, max_iters);
+    } else {
+        if constexpr (NODE) hist_node<Q, S>(blockIdx.x - nb_recon, Ih, gh, fh, slot, 0);
+        else hist_seg<Q, S>(blockIdx.x - nb_recon, Ih, gh, fh, slot, 0);
+    }
 }
 
 template <int Q, typename S>
 __global__ void __launch_bounds__(128) k_hist(IfaceDev I, LevelGeo gc, const S *__restrict__ fc, int slot, int seed)
 {
-    hist_body<Q, S>(blockIdx.x, I, gc, fc, slot, seed);
+    hist_node<Q, S>(blockIdx.x, I, gc, fc, slot, seed);
 }
 
-template <int Q, typename S>
+template <int Q, typename S, bool NODE>
 __global__ void __launch_bounds__(128) k_grad_ie(IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict__ ff,
                                                    TimeW tw, int sync, int nb_grad)
 {
-    if ((int)blockIdx.x < nb_grad) grad_body<Q, S>(blockIdx.x, I, F, Cl, ff, tw, sync);
-    else ie_body<Q, S>(blockIdx.x - nb_grad, I, F, ff);
+    if ((int)blockIdx.x < nb_grad) {
+        if constexpr (NODE) grad_node<Q, S>(blockIdx.x, I, F, Cl, ff, tw, sync);
+        else grad_seg<Q, S>(blockIdx.x, I, F, Cl, ff, tw, sync);
+    } else {
+        if constexpr (NODE) ie_node<Q, S>(blockIdx.x - nb_grad, I, F, ff);
+        else ie_seg<Q, S>(blockIdx.x - nb_grad, I, F, ff);
+    }
 }
 
 // ------------------------------------------------------------------ bulk collide-and-stream
@@ -1291,6 +1737,7 @@ struct BatchDev {
     const int *nb_recon;    // [L][n] Newton blocks of each hierarchy (the rest is history)
     const int *pre_gi;      // [L][n+1] prefix sums of (gradient + hanging) blocks
     const int *nb_grad;     // [L][n]
+    const int *node_rh, *node_gi;  // [L][n] one node per thread (1) or one segment per node (0)
     int *status, *max_iters;
     unsigned int *bar_count, *bar_gen;
     unsigned long long barrier_ns;  // a barrier wait longer than this gives up
@@ -1361,24 +1808,35 @@ template <int Q, typename S>
 __device__ __noinline__ void batch_recon_hist(const BatchDev &B, int h, int l, long long kl, int local, TimeW tw)
 {
     const int nbr = B.nb_recon[(size_t)l * B.n + h];
+    const bool node = B.node_rh[(size_t)l * B.n + h] != 0;
     const LevelDev &F = B.lev[h * B.L + l];
     const S *fA = (const S *)F.f[kl & 1];
-    if (local < nbr)
-        recon_body<Q, S>(local, B.ifc[h * B.L + l], F, B.lev[h * B.L + l - 1], fA, tw, (int)(kl & 1), B.status,
-                         B.max_iters);
-    else
-        hist_body<Q, S>(local - nbr, B.ifc[h * B.L + l + 1], F.g, fA, (int)((kl + 1) % 3), 0);
+    if (local < nbr) {
+        if (node)
+            recon_node<Q, S>(local, B.ifc[h * B.L + l], F, B.lev[h * B.L + l - 1], fA, tw, (int)(kl & 1), B.status,
+                             B.max_iters);
+        else
+            recon_seg<Q, S>(local, B.ifc[h * B.L + l], F, B.lev[h * B.L + l - 1], fA, tw, (int)(kl & 1), B.status,
+                            B.max_iters);
+    } else {
+        if (node) hist_node<Q, S>(local - nbr, B.ifc[h * B.L + l + 1], F.g, fA, (int)((kl + 1) % 3), 0);
+        else hist_seg<Q, S>(local - nbr, B.ifc[h * B.L + l + 1], F.g, fA, (int)((kl + 1) % 3), 0);
+    }
 }
 template <int Q, typename S>
 __device__ __noinline__ void batch_grad_ie(const BatchDev &B, int h, int l, long long kl, int local, TimeW tw)
 {
     const int nbg = B.nb_grad[(size_t)l * B.n + h];
+    const bool node = B.node_gi[(size_t)l * B.n + h] != 0;
     const LevelDev &F = B.lev[h * B.L + l];
     const S *fA = (const S *)F.f[kl & 1];
-    if (local < nbg)
-        grad_body<Q, S>(local, B.ifc[h * B.L + l], F, B.lev[h * B.L + l - 1], fA, tw, (int)(kl & 1));
-    else
-        ie_body<Q, S>(local - nbg, B.ifc[h * B.L + l], F, fA);
+    if (local < nbg) {
+        if (node) grad_node<Q, S>(local, B.ifc[h * B.L + l], F, B.lev[h * B.L + l - 1], fA, tw, (int)(kl & 1));
+        else grad_seg<Q, S>(local, B.ifc[h * B.L + l], F, B.lev[h * B.L + l - 1], fA, tw, (int)(kl & 1));
+    } else {
+        if (node) ie_node<Q, S>(local - nbg, B.ifc[h * B.L + l], F, fA);
+        else ie_seg<Q, S>(local - nbg, B.ifc[h * B.L + l], F, fA);
+    }
 }
 
 // Registers: at 80 registers per thread three 256-thread CTAs share an SM (a tighter

@@ -58,9 +58,10 @@ EXPORTS = [
     "lbm_timing_enable", "lbm_timing_read", "lbm_launch_count", "lbm_device_bytes", "lbm_synchronize",
     "lbm_last_error", "lbm_destroy", "lbm_reduce_static", "lbm_create_batch", "lbm_batch_member",
     "lbm_batch_check_barrier", "lbm_set_probes", "lbm_get_probes", "lbm_save_state", "lbm_load_state",
-    "lbm_autotune", "lbm_set_tile_config", "lbm_get_tile_config",
+    "lbm_autotune", "lbm_set_tile_config", "lbm_get_tile_config", "lbm_set_interface_mapping",
 ]
 TILE_CONFIGS = 5
+IFACE_AUTO, IFACE_NODE, IFACE_SEGMENT = 0, 1, 2
 
 _lib = None
 
@@ -107,6 +108,7 @@ def lib():
     L.lbm_load_state.argtypes = [vp, vp, C.c_size_t]
     L.lbm_autotune.argtypes = [vp, C.c_int, dp]
     L.lbm_set_tile_config.argtypes = [vp, C.c_int, C.c_int]
+    L.lbm_set_interface_mapping.argtypes = [vp, C.c_int]
     L.lbm_get_tile_config.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
     _lib = L
     return L
@@ -311,6 +313,11 @@ class Hierarchy:
 
     def set_tile_config(self, level, cfg):
         self._check(lib().lbm_set_tile_config(self._h, level, int(cfg)))
+
+    def set_interface_mapping(self, mode):
+        """IFACE_AUTO, IFACE_NODE (one interface node per thread) or IFACE_SEGMENT (one
+        warp segment per node)."""
+        self._check(lib().lbm_set_interface_mapping(self._h, int(mode)))
 
     def tile_config(self, level):
         c = C.c_int()

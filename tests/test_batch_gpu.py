@@ -1,7 +1,7 @@
 """Batched hierarchies advanced by one persistent cooperative launch: every member
-matches the same hierarchy advanced alone (bitwise: the same device arithmetic per
-node and per interface segment) and the FP64 oracle; the grid barrier's bounded wait
-reports a timeout instead of hanging."""
+matches the same hierarchy advanced alone with the batch's interface mapping (one
+node per thread; bitwise: the same device arithmetic per node) and the FP64 oracle;
+the grid barrier's bounded wait reports a timeout instead of hanging."""
 import numpy as np
 import pytest
 
@@ -27,6 +27,7 @@ def test_batch_members_equal_individual_runs(storage):
     singles = []
     for d, m in zip(descs, b.members):
         s = lbm.Hierarchy(d)
+        s.set_interface_mapping(lbm.IFACE_NODE)
         for l in range(m.n_levels):
             r, u = W.init_fields(d, l)
             m.init_fields(l, r, u)

@@ -326,3 +326,39 @@ def test_d3q19_every_chunking_gives_identical_results():
         g.advance(3)
         for l in range(g.n_levels):
             assert np.array_equal(g.get_pops(l), ref.get_pops(l)), (c, l)
+
+
+# The interface kernels have two thread mappings (one node per thread for large
+# interfaces, one warp segment per node for small ones; AUTO picks by size, so the
+# small cases above run segments).  Both must match the oracle.
+@pytest.mark.parametrize("mapping", [lbm.IFACE_NODE, lbm.IFACE_SEGMENT])
+@pytest.mark.parametrize("case", ["vortex2d", "pulse3lvl", "d3q19"])
+def test_interface_mappings_against_oracle_f64(case, mapping):
+    if case == "vortex2d":
+        d, n = W.vortex2d(), 40
+    elif case == "pulse3lvl":
+        d, n = W.pulse2d(n=64, boxes=((16, 48), (24, 40)), Rc_finest=3.0), 12
+    else:
+        d, n = D3_WIDE, 4
+    g = lbm.Hierarchy(d)
+    g.set_interface_mapping(mapping)
+    o = O.Hierarchy(d)
+    for l in range(g.n_levels):
+        r, u = W.init_fields(d, l)
+        g.init_fields(l, r, u)
+        o.init(l, r, u)
+    g.advance(n)
+    o.advance(n)
+    _assert_parity(g, o, 1e-12)
+
+
+def test_interface_mappings_agree_f32():
+    d = dict(D3_WIDE, storage="f32")
+    out = []
+    for mapping in (lbm.IFACE_NODE, lbm.IFACE_SEGMENT):
+        g, _ = _pair(d)
+        g.set_interface_mapping(mapping)
+        g.advance(4)
+        out.append([g.get_macros(l) for l in range(g.n_levels)])
+    for (r0, u0), (r1, u1) in zip(*out):
+        assert np.max(np.abs(r0 - r1)) < 1e-6 and np.max(np.abs(u0 - u1)) < 1e-6
