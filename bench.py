@@ -248,6 +248,9 @@ def run_batch(args):
         "e2e": None,
     }
     b.close()
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline("batch2d", args.cpu_steps)
+        line["accuracy"] = accuracy("batch2d", [storage])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -463,9 +466,10 @@ def run_gb300(args):
         "variants": variants,
         "bulk_at_scale": scale,
     }
-    if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
     h.close()
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_steps)
+        line["accuracy"] = accuracy(args.workload, [main_storage] + [x for x in variants if "speedup" not in x])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -474,60 +478,131 @@ def run_gb300(args):
         dist.destroy_process_group()
 
 
-def _replica_desc():
-    """The 1/16-size replica of the benchmark workload (128^2 coarse, same
-    proportions and physics) on which the CPU oracle is timed."""
+# Bounded samples for the oracle (CPU baseline, reference arm, accuracy): a replica of
+# each workload with the same proportions and physics, and the coarse steps that keep
+# the single-threaded oracle within ~10-30 s.
+REPLICA = {
+    "pulse2d_3lvl": ("128^2 three-level replica (1/4 of each axis)", 150, 40),
+    "vortex2d_2lvl": ("the workload itself (128^2, two levels)", 150, 40),
+    "vortex3d_3lvl": ("32^3 three-level replica (1/8 of each axis)", 15, 6),
+    "vortex3d_3lvl_128": ("32^3 three-level replica (1/8 of vortex3d_3lvl per axis)", 15, 6),
+    "slab3d_3lvl": ("64x64x32 three-level replica (1/8 of each axis)", 3, 2),
+    "batch2d": ("one 128^2 two-level member", 150, 40),
+}
+
+
+def _replica_desc(workload="pulse2d_3lvl", storage="f64"):
+    """The replica of a workload on which the oracle is timed and compared."""
     from paper_2004_14887_gb300 import workloads as W
 
-    return W.pulse2d(n=128, boxes=((32, 96), (48, 80)), steps=20)
+    if workload in ("vortex3d_3lvl", "vortex3d_3lvl_128"):
+        return W.vortex3d(n=32, boxes=((8, 24), (12, 20)), storage=storage)
+    if workload == "slab3d_3lvl":
+        return W.slab3d(nxy=64, nz=32, slab=(12, 20), box=((16, 16, 14), (48, 48, 18)), storage=storage)
+    if workload == "vortex2d_2lvl":
+        return W.vortex2d(storage=storage)
+    if workload == "batch2d":
+        return W.batch2d(n=1, sides=(128,), storage=storage)[0]
+    return W.pulse2d(n=128, boxes=((32, 96), (48, 80)), steps=20, storage=storage)
 
 
-def cpu_baseline(steps):
+def _oracle_run(workload, steps, warm=1):
     from oracle import oracle as O
     from paper_2004_14887_gb300 import workloads as W
 
-    d = _replica_desc()
+    d = _replica_desc(workload)
     o = O.Hierarchy(d)
     for l in range(o.n_levels):
         r, u = W.init_fields(d, l)
         o.init(l, r, u)
-    o.advance(1)
+    o.advance(warm)
     t0 = time.perf_counter()
     o.advance(steps)
-    dt = time.perf_counter() - t0
+    return d, o, time.perf_counter() - t0
+
+
+def cpu_baseline(workload, steps=None):
+    from paper_2004_14887_gb300 import workloads as W
+
+    text, default_steps, _ = REPLICA[workload]
+    steps = steps or default_steps
+    d, _, dt = _oracle_run(workload, steps)
     feq = W.fine_equivalent_per_coarse_step(d)
     return {"value": feq * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} coarse steps of the 128^2 three-level replica of the workload "
+            "sample": f"{steps} coarse steps of the {text} of the workload "
                       f"({W.updates_per_coarse_step(d)} node updates per step), single-threaded FP64 oracle",
             "actual_mlups": W.updates_per_coarse_step(d) * steps / dt / 1e6}
 
 
+# pressure scale of the Pa-equivalent error: p' = (rho'/rho0) rho0 c0^2 with
+# rho0 c0^2 = 1.206e5 Pa (air at rest)
+P_REF_PA = 1.206e5
+
+
+def accuracy(workload, storages):
+    """The workload's replica advanced on the GPU in each storage and by the FP64
+    oracle for the same steps: per storage, the relative L-infinity errors of rho and
+    u (worst level), the density error relative to the signal amplitude max|rho - 1|,
+    and the RMS density error as a pressure in Pa-equivalent."""
+    import numpy as np
+
+    from paper_2004_14887_gb300 import lbm
+    from paper_2004_14887_gb300 import workloads as W
+
+    text, _, steps = REPLICA[workload]
+    d64, o, _ = _oracle_run(workload, steps, warm=0)
+    ref = [o.macros(l) for l in range(o.n_levels)]
+    out = {}
+    for st in storages:
+        d = dict(d64, storage=st)
+        g = lbm.Hierarchy(d)
+        for l in range(g.n_levels):
+            r, u = W.init_fields(d, l)
+            g.init_fields(l, r, u)
+        g.advance(steps)
+        g.check_status()
+        er = eu = ed = 0.0
+        sq, cnt, amp = 0.0, 0, 0.0
+        for l in range(g.n_levels):
+            m = g.node_class(l) != lbm.HOLE
+            rg, ug = g.get_macros(l)
+            ro, uo = ref[l]
+            amp = max(amp, float(np.max(np.abs(ro[m] - 1.0))))
+            dr = rg[m] - ro[m]
+            er = max(er, float(np.max(np.abs(dr)) / np.max(np.abs(ro[m]))))
+            eu = max(eu, float(np.max(np.abs(ug[:, m] - uo[:, m])) / max(np.max(np.abs(uo[:, m])), 1e-300)))
+            ed = max(ed, float(np.max(np.abs(dr))))
+            sq += float(np.sum(dr * dr))
+            cnt += int(m.sum())
+        g.close()
+        rms = (sq / max(cnt, 1)) ** 0.5
+        out[st] = {"rho_rel_linf": er, "u_rel_linf": eu, "drho_rel_amplitude": ed / max(amp, 1e-300),
+                   "dp_rms_pa": rms * P_REF_PA, "dp_max_pa": ed * P_REF_PA, "amplitude_pa": amp * P_REF_PA}
+    return {"vs": "FP64 oracle", "sample": f"{steps} coarse steps of the {text}", "by_storage": out}
+
+
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle timed on a bounded sample of the same
+    workload (its replica), on rank 0 only."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    from oracle import oracle as O
     from paper_2004_14887_gb300 import workloads as W
 
-    d = _replica_desc()
-    o = O.Hierarchy(d)
-    for l in range(o.n_levels):
-        r, u = W.init_fields(d, l)
-        o.init(l, r, u)
-    o.advance(args.warmup)
-    K = args.steps
-    t0 = time.perf_counter()
-    o.advance(K)
-    dt = time.perf_counter() - t0
+    text, cpu_steps, _ = REPLICA[args.workload]
+    # the oracle's steps are bounded so that the arm ends within minutes (3-D replicas
+    # take about a second per coarse step)
+    cap = 2000 if cpu_steps >= 100 else 2 * cpu_steps
+    K = min(args.steps, cap)
+    d, _, dt = _oracle_run(args.workload, K, warm=min(args.warmup, max(1, cap // 20)))
     feq = W.fine_equivalent_per_coarse_step(d)
     v = feq * K / dt / 1e6
+    sample = f"{K} coarse steps of the {text} of the workload, single-threaded FP64 oracle"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": K,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / K, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded analytic pulse, no dataset)",
-            "config": {"workload": "pulse2d_3lvl replica: D2Q9, 3 levels, coarse 128^2, patches 64^2 and 32^2 coarse "
-                                   "cells (1/16 of the 512^2 workload, same proportions and physics)"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{K} coarse steps of the 128^2 replica, single-threaded FP64 oracle"},
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded analytic fields, no dataset)",
+            "config": {"workload": WORKLOAD_TEXT[args.workload], "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -541,7 +616,7 @@ def main():
     ap.add_argument("--workload", default="pulse2d_3lvl", choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--storage", default=None, choices=["f64", "f32", "f16s"])
     ap.add_argument("--variant-steps", type=int, default=400)
-    ap.add_argument("--cpu-steps", type=int, default=150)
+    ap.add_argument("--cpu-steps", type=int, default=None, help="oracle steps of the CPU baseline (default per workload)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
