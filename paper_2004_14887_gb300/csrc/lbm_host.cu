@@ -76,6 +76,10 @@ struct lbm_hierarchy {
     Iface ifc[LBM_MAX_LEVELS];  // ifc[l] couples level l-1 and level l (l >= 1)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // second stream: a level's TF-gradient / hanging-node launch runs beside its child
+    // level's sub-steps (fork and join events per level; captured as graph branches)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork[LBM_MAX_LEVELS] = {}, ev_join[LBM_MAX_LEVELS] = {};
     std::vector<DevBuf> bufs;
     int64_t device_bytes = 0;
     int *d_status = nullptr, *d_maxit = nullptr;
@@ -986,24 +990,39 @@ struct Sched {
                                                                             (const S *)fA, (int)((k + 1) % 3));
             h->launch_counter++;
         }
-        if (l + 1 < h->nl) {
-            level_step(h, l + 1, 2 * k, 0, k);
-            level_step(h, l + 1, 2 * k + 1, 1, k);
-        }
+        // TF gradients and hanging nodes of this level read this level's populations, TF
+        // rows and ring history and write this level's TF and hanging rows; the child
+        // level's sub-steps touch only the child's data, the history of the child
+        // interface and this level's child-TF rows.  So with a child the launch runs on
+        // the side stream beside the child's sub-steps; the bulk launch joins both.
+        bool forked = false;
         if (l > 0) {
             const IfaceDev &I = h->ifc[l].dev;
             const int per = per_block(I.nTF + I.nIE);
             const int nbg = (I.nTF + per - 1) / per, nbi = (I.nIE + per - 1) / per;
             if (nbg + nbi > 0) {
+                cudaStream_t st = h->stream;
+                if (l + 1 < h->nl) {
+                    cudaEventRecord(h->ev_fork[l], h->stream);
+                    cudaStreamWaitEvent(h->side, h->ev_fork[l], 0);
+                    st = h->side;
+                    forked = true;
+                }
                 if (per == 128)
-                    k_grad_ie<Q, S, true><<<nbg + nbi, 128, 0, h->stream>>>(I, dv, level_dev(h, l - 1), (const S *)fA,
-                                                                            tw, phase, nbg);
+                    k_grad_ie<Q, S, true><<<nbg + nbi, 128, 0, st>>>(I, dv, level_dev(h, l - 1), (const S *)fA, tw,
+                                                                     phase, nbg);
                 else
-                    k_grad_ie<Q, S, false><<<nbg + nbi, 128, 0, h->stream>>>(I, dv, level_dev(h, l - 1), (const S *)fA,
-                                                                             tw, phase, nbg);
+                    k_grad_ie<Q, S, false><<<nbg + nbi, 128, 0, st>>>(I, dv, level_dev(h, l - 1), (const S *)fA, tw,
+                                                                      phase, nbg);
                 h->launch_counter++;
+                if (forked) cudaEventRecord(h->ev_join[l], h->side);
             }
         }
+        if (l + 1 < h->nl) {
+            level_step(h, l + 1, 2 * k, 0, k);
+            level_step(h, l + 1, 2 * k + 1, 1, k);
+        }
+        if (forked) cudaStreamWaitEvent(h->stream, h->ev_join[l], 0);
         bulk(h, l, fA, fB);
     }
 
@@ -1162,6 +1181,15 @@ int lbm_create_hierarchy(const lbm_hierarchy_desc *desc, void *cuda_stream, lbm_
             return fail(nullptr, LBM_ERR_CUDA, "cudaStreamCreateWithFlags failed");
         }
         h->own_stream = true;
+    }
+    bool evok = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) == cudaSuccess;
+    for (int l = 0; l < LBM_MAX_LEVELS && evok; l++)
+        evok = cudaEventCreateWithFlags(&h->ev_fork[l], cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&h->ev_join[l], cudaEventDisableTiming) == cudaSuccess;
+    if (!evok) {
+        g_create_error = "cudaStreamCreateWithFlags / cudaEventCreateWithFlags failed";
+        lbm_destroy(h);
+        return LBM_ERR_CUDA;
     }
     rc = upload_all(h);
     if (rc != LBM_OK) {
@@ -1393,6 +1421,14 @@ void lbm_destroy(lbm_h h)
     for (auto &b : h->bufs) {
         if (h->d.free) h->d.free(b.p, h->d.alloc_ctx);
         else cudaFree(b.p);
+    }
+    if (h->side) {
+        cudaStreamSynchronize(h->side);
+        cudaStreamDestroy(h->side);
+    }
+    for (int l = 0; l < LBM_MAX_LEVELS; l++) {
+        if (h->ev_fork[l]) cudaEventDestroy(h->ev_fork[l]);
+        if (h->ev_join[l]) cudaEventDestroy(h->ev_join[l]);
     }
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
