@@ -32,7 +32,20 @@ if ROOT not in sys.path:
 
 METRIC = "MLUPS (fine-equiv) & % HBM roofline, FP32/FP16-shift vs FP64 on same GB300"
 UNIT = "MLUPS (fine-equivalent)"
-BYTES_PER_POP = {"f64": 8, "f32": 4, "f16s": 2}
+BYTES_PER_POP = {"f64": 8, "f32": 4, "f16s": 2, "f16s_mean": 2}
+
+
+def _with_storage(d, storage):
+    """A description in one of the reported storage forms: f64, f32, f16s (half of
+    f_i - w_i) or f16s_mean (half of f_i - f_i^eq(1, U), U the workload's mean flow)."""
+    d = dict(d)
+    if storage == "f16s_mean":
+        d["storage"] = "f16s"
+        d["u_shift"] = tuple(d["init"]["U"])
+    else:
+        d["storage"] = storage
+        d.pop("u_shift", None)
+    return d
 
 
 def _peaks():
@@ -190,7 +203,7 @@ def run_batch(args):
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     storage = args.storage or DEFAULT_STORAGE["batch2d"]
-    descs = W.batch2d(storage=storage)
+    descs = [_with_storage(d, storage) for d in W.batch2d()]
     tc = time.perf_counter()
     b = lbm.Batch(descs)
     for d, m in zip(descs, b.members):
@@ -286,7 +299,7 @@ def run_gb300(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
 
     def make(storage, use_graphs=True):
-        d = WORKLOADS[args.workload](storage=storage)
+        d = _with_storage(WORKLOADS[args.workload](), storage)
         tc = time.perf_counter()
         h = lbm.Hierarchy(d, use_graphs=use_graphs)
         print(f"[bench] {args.workload} {storage}: set-up {time.perf_counter() - tc:.2f} s, "
@@ -359,7 +372,7 @@ def run_gb300(args):
     # reduced / full precision variants on the same workload
     variants = {}
     if not args.no_variants:
-        for st in [x for x in ("f64", "f32", "f16s") if x != main_storage]:
+        for st in [x for x in ("f64", "f32", "f16s", "f16s_mean") if x != main_storage]:
             dv, hv = make(st)
             Kv = min(K, args.variant_steps if st == "f64" else K)
             dms, _, _, _ = timed(hv, Kv, max(3, Wm // 2))
@@ -380,7 +393,7 @@ def run_gb300(args):
             del hv
         vals = dict(variants)
         vals[main_storage] = {"value": value}
-        for st in ("f32", "f16s"):
+        for st in ("f32", "f16s", "f16s_mean"):
             if st in vals and "f64" in vals:
                 variants[f"{st}_speedup_vs_f64"] = vals[st]["value"] / vals["f64"]["value"]
 
@@ -418,7 +431,7 @@ def run_gb300(args):
     # end the macros of every level (D2H)
     e2e = None
     if not args.no_e2e:
-        de = WORKLOADS[args.workload](storage=main_storage)
+        de = _with_storage(WORKLOADS[args.workload](), main_storage)
         he = lbm.Hierarchy(de)
         fields = []
         for l in range(he.n_levels):
@@ -561,7 +574,7 @@ def accuracy(workload, storages):
     ref = [o.macros(l) for l in range(o.n_levels)]
     out = {}
     for st in storages:
-        d = dict(d64, storage=st)
+        d = _with_storage(d64, st)
         g = lbm.Hierarchy(d)
         for l in range(g.n_levels):
             r, u = W.init_fields(d, l)
@@ -621,7 +634,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="pulse2d_3lvl", choices=sorted(WORKLOAD_TEXT))
-    ap.add_argument("--storage", default=None, choices=["f64", "f32", "f16s"])
+    ap.add_argument("--storage", default=None, choices=["f64", "f32", "f16s", "f16s_mean"])
     ap.add_argument("--variant-steps", type=int, default=400)
     ap.add_argument("--cpu-steps", type=int, default=None, help="oracle steps of the CPU baseline (default per workload)")
     ap.add_argument("--no-variants", action="store_true")

@@ -83,13 +83,19 @@ typedef void (*lbm_free_fn)(void *ptr, void *ctx);
  *   sigma       H-RR hybridisation weight of Eq. (a12_HRR) (0.98 in the paper).
  *   dc_variant  2 = DC2 of Table 1 (coarse data on P and M^f); 1 = DC1 (coarse on M^f only).
  *   storage     LBM_F64 (FP64 storage and arithmetic), LBM_F32 (FP32 storage and
- *               arithmetic), LBM_F16S (IEEE half storing f_i - w_i, FP32 arithmetic).
- *               Interface reconstruction (Newton, rescaling, interpolation) is FP64
- *               in every mode.
+ *               arithmetic), LBM_F16S (IEEE half storing f_i - s_i, FP32 arithmetic,
+ *               s_i below).  The equilibrium / non-equilibrium rescalings of Eqs.
+ *               (rescff) and (rescfc) are FP64 in every mode; the Newton solve runs
+ *               in the arithmetic type.
  *   psi_sign    +1/-1 factor on the cubic-Mach correction psi_i of App. A; -1 makes
  *               the correction cancel the rho u^3 defect with Psi as printed.
  *   use_graphs  nonzero: lbm_advance replays one captured CUDA graph per coarse step.
  *   alloc/free/alloc_ctx  optional device allocator (both or neither).
+ *   u_shift     LBM_F16S only: the shift of the stored deviation is the equilibrium
+ *               s_i = f_i^eq(1, u_shift) of Eq. (fEq_herm); {0, 0, 0} gives s_i = w_i
+ *               (f_i - w_i).  A u_shift near the flow's mean velocity leaves only the
+ *               perturbation to half precision.  A saved state must be loaded into a
+ *               hierarchy with the same u_shift.  Components below 0.3 in magnitude.
  */
 typedef struct {
     int lattice;
@@ -106,6 +112,7 @@ typedef struct {
     lbm_alloc_fn alloc;
     lbm_free_fn free;
     void *alloc_ctx;
+    double u_shift[3];
 } lbm_hierarchy_desc;
 
 typedef struct lbm_hierarchy *lbm_h;

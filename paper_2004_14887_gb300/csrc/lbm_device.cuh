@@ -115,6 +115,7 @@ struct LevelGeo {
     int n[3];
     int per[3];
     int px;           // row pitch in slots: n[0] padded to a multiple of 8
+    float shift[19];  // FP16-shifted storage keeps f_i - shift[i] (f_i^eq(1, u_shift))
     long long N;      // box nodes n[0] n[1] n[2] (dense order of the host arrays)
     long long NS;     // slots px n[1] n[2] of the tag map and population planes
     long long pitch;  // elements between population planes (>= NS)
@@ -304,7 +305,7 @@ __device__ __forceinline__ void hrr_collide(R (&f)[Q], R rho, const R *u, const 
 
 // Equilibrium of Eq. (fEq_herm) of population i
 template <int Q>
-__device__ __forceinline__ double feq_one(int i, double rho, const double *u)
+__host__ __device__ __forceinline__ double feq_one(int i, double rho, const double *u)
 {
     using L = Lat<Q>;
     constexpr int D = L::D;

@@ -84,6 +84,7 @@ struct lbm_hierarchy {
     int64_t device_bytes = 0;
     int *d_status = nullptr, *d_maxit = nullptr;
     int if_mode = LBM_IFACE_AUTO;  // interface thread mapping (lbm_set_interface_mapping)
+    float shift[19] = {};          // FP16-shifted storage: f_i - shift[i] (f_i^eq(1, u_shift))
     double *d_partial = nullptr, *d_red = nullptr;
     int red_blocks = 0;
     long long ncoarse = 0;  // coarse steps done since init
@@ -860,6 +861,7 @@ LevelDev level_dev(const lbm_h h, int l)
     }
     d.g.N = v.N;
     d.g.px = (int)v.px;
+    for (int i = 0; i < 19; i++) d.g.shift[i] = h->shift[i];
     d.g.NS = v.NS;
     d.g.pitch = v.pitch;
     d.f[0] = v.f[0];
@@ -1146,6 +1148,9 @@ int lbm_create_hierarchy(const lbm_hierarchy_desc *desc, void *cuda_stream, lbm_
         return fail(nullptr, LBM_ERR_BAD_DESC, "nu0 must be > 0 and sigma in [0,1]");
     if ((desc->alloc == nullptr) != (desc->free == nullptr)) return fail(nullptr, LBM_ERR_BAD_DESC, "alloc and free go together");
     const int D = desc->lattice == 9 ? 2 : 3;
+    for (int a = 0; a < 3; a++)
+        if (!(std::fabs(desc->u_shift[a]) < 0.3) || (a >= D && desc->u_shift[a] != 0.0))
+            return fail(nullptr, LBM_ERR_BAD_DESC, "u_shift components must be below 0.3 (0 beyond the lattice's dimension)");
     for (int a = 0; a < 3; a++) {
         if (desc->coarse_n[a] < 1 || desc->coarse_n[a] > (1 << 20)) return fail(nullptr, LBM_ERR_BAD_DESC, "coarse_n out of range");
         if (a >= D && desc->coarse_n[a] != 1) return fail(nullptr, LBM_ERR_BAD_DESC, "coarse_n[2] must be 1 for D2Q9");
@@ -1156,6 +1161,8 @@ int lbm_create_hierarchy(const lbm_hierarchy_desc *desc, void *cuda_stream, lbm_
     h->Q = desc->lattice;
     h->D = D;
     h->nl = desc->n_levels;
+    for (int i = 0; i < h->Q; i++)  // s_i = f_i^eq(1, u_shift): w_i for u_shift = 0
+        h->shift[i] = (float)(h->Q == 9 ? feq_one<9>(i, 1.0, desc->u_shift) : feq_one<19>(i, 1.0, desc->u_shift));
     int rc = build_geometry(h);
     if (rc == LBM_OK) rc = build_interfaces(h);
     if (rc != LBM_OK) {

@@ -101,7 +101,7 @@ __device__ __forceinline__ void pulled_moments(const LevelGeo &g, const S *__res
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         const int s = nb_index(g, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
-        const R v = s >= 0 ? St<S>::ld(f, (long long)i * g.pitch + s, L::w(i)) : R(0);
+        const R v = s >= 0 ? St<S>::ld(f, (long long)i * g.pitch + s, g.shift[i]) : R(0);
         r += v;
 #pragma unroll
         for (int a = 0; a < D; a++)
@@ -110,6 +110,18 @@ __device__ __forceinline__ void pulled_moments(const LevelGeo &g, const S *__res
     rho = r;
 #pragma unroll
     for (int a = 0; a < 3; a++) u[a] = a < D ? m[a] / r : R(0);
+}
+
+// storage shift of a run-time population index (FP16-shifted storage; compile-time
+// indices into the shift table, no local copy of the kernel parameter)
+template <int Q>
+__device__ __forceinline__ float lane_shift(const LevelGeo &g, int i)
+{
+    float s = 0.0f;
+#pragma unroll
+    for (int j = 0; j < Q; j++)
+        if (i == j) s = g.shift[j];
+    return s;
 }
 
 // ------------------------------------------------------------------ interface nodes, W-lane segments
@@ -327,7 +339,7 @@ __device__ __forceinline__ void recon_seg(int bid, IfaceDev I, LevelDev F, Level
         } else {
             if ((I.tf_kf[t] >> i) & 1u) {
                 const int s = nb_index(F.g, I.tf_f[3 * t], I.tf_f[3 * t + 1], I.tf_f[3 * t + 2], -c[0], -c[1], -c[2]);
-                if (s >= 0) fhat = St<S>::ld(ff, (long long)i * F.g.pitch + s, wd);
+                if (s >= 0) fhat = St<S>::ld(ff, (long long)i * F.g.pitch + s, lane_shift<Q>(F.g, i));
             }
             gam = R(1);
         }
@@ -388,13 +400,13 @@ __device__ __forceinline__ void hist_seg(int bid, IfaceDev I, LevelGeo gc, const
         const int s = seed ? box_index(gc, x, y, z)
                            : (((I.tf_kc[t] >> i) & 1u) ? nb_index(gc, x, y, z, -c[0], -c[1], -c[2]) : -1);
         ((R *)I.hist_f)[((long long)slot * Q + i) * I.nTF + t] =
-            s >= 0 ? St<S>::ld(fc, (long long)i * gc.pitch + s, wd) : R(0);
+            s >= 0 ? St<S>::ld(fc, (long long)i * gc.pitch + s, lane_shift<Q>(gc, i)) : R(0);
     }
     R v = R(0);
     if (live_ring && i < Q) {
         const int x = I.ring_c[3 * r], y = I.ring_c[3 * r + 1], z = I.ring_c[3 * r + 2];
         const int s = seed ? box_index(gc, x, y, z) : nb_index(gc, x, y, z, -c[0], -c[1], -c[2]);
-        if (s >= 0) v = St<S>::ld(fc, (long long)i * gc.pitch + s, wd);
+        if (s >= 0) v = St<S>::ld(fc, (long long)i * gc.pitch + s, lane_shift<Q>(gc, i));
     }
     const R rho = seg_sum<W>(v);
     R m[3] = {R(0), R(0), R(0)};
@@ -452,7 +464,7 @@ __device__ __forceinline__ void grad_seg(int bid, IfaceDev I, LevelDev F, LevelD
             if (live && kd == RK_FINE && i < Q) {
                 const int x = rf % F.g.n[0], yz = rf / F.g.n[0];
                 const int src = nb_index(F.g, x, yz % F.g.n[1], yz / F.g.n[1], -c[0], -c[1], -c[2]);
-                if (src >= 0) v[b][s] = St<S>::ld(ff, (long long)i * F.g.pitch + src, wd);
+                if (src >= 0) v[b][s] = St<S>::ld(ff, (long long)i * F.g.pitch + src, lane_shift<Q>(F.g, i));
             }
             rho[b][s] = R(0);
 #pragma unroll
@@ -526,7 +538,7 @@ __device__ __forceinline__ void ie_seg(int bid, IfaceDev I, LevelDev F, const S 
     if (live && i < Q) {
         if ((I.ie_kf[e] >> i) & 1u) {
             const int s = nb_index(F.g, I.ie_f[3 * e], I.ie_f[3 * e + 1], I.ie_f[3 * e + 2], -c[0], -c[1], -c[2]);
-            if (s >= 0) v = St<S>::ld(ff, (long long)i * F.g.pitch + s, wd);
+            if (s >= 0) v = St<S>::ld(ff, (long long)i * F.g.pitch + s, lane_shift<Q>(F.g, i));
         } else {
             const R *iw = (const R *)I.ie_w;
             for (int k = 0; k < nst; k++) v += iw[e * 16 + k] * fpop[(long long)i * nif + I.ie_st[e * 16 + k]];
@@ -760,7 +772,7 @@ __device__ __forceinline__ void recon_node(int bid, IfaceDev I, LevelDev F, Leve
                 if ((tw.nz >> k) & 1) v += tw_w<R>(tw, k) * hf[((long long)tw.slot[k] * Q + i) * I.nTF + t];
         } else if ((kfm >> i) & 1u) {
             const int s = nb_index(F.g, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
-            if (s >= 0) v = St<S>::ld(ff, (long long)i * F.g.pitch + s, L::w(i));
+            if (s >= 0) v = St<S>::ld(ff, (long long)i * F.g.pitch + s, F.g.shift[i]);
         }
         fhat[i] = v;
     });
@@ -820,7 +832,7 @@ __device__ __forceinline__ void hist_node(int bid, IfaceDev I, LevelGeo gc, cons
             constexpr int i = decltype(ic)::value;
             const int s = seed ? box_index(gc, x, y, z)
                                : (((kcm >> i) & 1u) ? nb_index(gc, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2)) : -1);
-            hf[((long long)slot * Q + i) * I.nTF + t] = s >= 0 ? St<S>::ld(fc, (long long)i * gc.pitch + s, L::w(i)) : R(0);
+            hf[((long long)slot * Q + i) * I.nTF + t] = s >= 0 ? St<S>::ld(fc, (long long)i * gc.pitch + s, gc.shift[i]) : R(0);
         });
     } else if (item < I.nTF + I.nRing) {
         const int r = item - I.nTF;
@@ -829,7 +841,7 @@ __device__ __forceinline__ void hist_node(int bid, IfaceDev I, LevelGeo gc, cons
         static_for<Q>([&](auto ic) {
             constexpr int i = decltype(ic)::value;
             const int s = seed ? box_index(gc, x, y, z) : nb_index(gc, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
-            const R v = s >= 0 ? St<S>::ld(fc, (long long)i * gc.pitch + s, L::w(i)) : R(0);
+            const R v = s >= 0 ? St<S>::ld(fc, (long long)i * gc.pitch + s, gc.shift[i]) : R(0);
             rho += v;
             static_for<D>([&](auto ac) {
                 constexpr int a = decltype(ac)::value;
@@ -884,7 +896,7 @@ __device__ __forceinline__ void grad_node(int bid, IfaceDev I, LevelDev F, Level
                 static_for<Q>([&](auto ic) {
                     constexpr int i = decltype(ic)::value;
                     const int src = nb_index(F.g, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
-                    const R v = src >= 0 ? St<S>::ld(ff, (long long)i * F.g.pitch + src, L::w(i)) : R(0);
+                    const R v = src >= 0 ? St<S>::ld(ff, (long long)i * F.g.pitch + src, F.g.shift[i]) : R(0);
                     r += v;
                     static_for<D>([&](auto ac) {
                         constexpr int a = decltype(ac)::value;
@@ -953,7 +965,7 @@ __device__ __forceinline__ void ie_node(int bid, IfaceDev I, LevelDev F, const S
         R v = R(0);
         if ((kfm >> i) & 1u) {
             const int s = nb_index(F.g, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
-            if (s >= 0) v = St<S>::ld(ff, (long long)i * F.g.pitch + s, L::w(i));
+            if (s >= 0) v = St<S>::ld(ff, (long long)i * F.g.pitch + s, F.g.shift[i]);
         } else {
             for (int k = 0; k < nst; k++) v += iw[e * 16 + k] * fpop[(long long)i * nif + I.ie_st[e * 16 + k]];
         }
@@ -1115,7 +1127,7 @@ __device__ __forceinline__ void collide_store(const LevelDev &Lv, typename St<S>
     hrr_collide<Q, R>(f, rho, u, Sv, Cv, tau, om, sigma, spsi);
     static_for<Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
-        St<S>::st(fdst + (long long)i * Lv.g.pitch, idx, f[i], L::w(i));
+        St<S>::st(fdst + (long long)i * Lv.g.pitch, idx, f[i], Lv.g.shift[i]);
     });
 }
 
@@ -1197,13 +1209,13 @@ __device__ __forceinline__ bool bulk2d_tile(const LevelDev &Lv, const S *__restr
             const S *pi = fsrc + (long long)i * g.pitch;  // population plane
             const int off = L::c(i, 0) + g.px * L::c(i, 1);
 #pragma unroll
-            for (int r = 0; r < NR; r++) f[r][i] = St<S>::ld(pi, idx[r] - off, L::w(i));
+            for (int r = 0; r < NR; r++) f[r][i] = St<S>::ld(pi, idx[r] - off, g.shift[i]);
         }
         if (hb >= 0) {
 #pragma unroll
             for (int i = 0; i < Q; i++) {
                 const int off = L::c(i, 0) + g.px * L::c(i, 1);
-                fh[i] = St<S>::ld(fsrc + (long long)i * g.pitch, hidx - off, L::w(i));
+                fh[i] = St<S>::ld(fsrc + (long long)i * g.pitch, hidx - off, g.shift[i]);
             }
         }
     } else {
@@ -1230,13 +1242,13 @@ __device__ __forceinline__ bool bulk2d_tile(const LevelDev &Lv, const S *__restr
                 int sx = ox[r] - L::c(i, 0), sy = oy[r] - L::c(i, 1);
                 sx += (sx < 0) ? g.n[0] : ((sx >= g.n[0]) ? -g.n[0] : 0);
                 sy += (sy < 0) ? g.n[1] : ((sy >= g.n[1]) ? -g.n[1] : 0);
-                f[r][i] = otag[r] == TAG_BULK ? St<S>::ld(pi, sx + g.px * sy, L::w(i))
+                f[r][i] = otag[r] == TAG_BULK ? St<S>::ld(pi, sx + g.px * sy, g.shift[i])
                                               : (otag[r] >= 0 ? pop[(long long)i * Lv.nif + otag[r]] : R(0));
             }
             int hsx = qx - L::c(i, 0), hsy = qy - L::c(i, 1);
             hsx += (hsx < 0) ? g.n[0] : ((hsx >= g.n[0]) ? -g.n[0] : 0);
             hsy += (hsy < 0) ? g.n[1] : ((hsy >= g.n[1]) ? -g.n[1] : 0);
-            fh[i] = htag == TAG_BULK ? St<S>::ld(pi, hsx + g.px * hsy, L::w(i))
+            fh[i] = htag == TAG_BULK ? St<S>::ld(pi, hsx + g.px * hsy, g.shift[i])
                                      : (htag >= 0 ? pop[(long long)i * Lv.nif + htag] : R(0));
         }
     }
@@ -1591,7 +1603,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
             if (tn == TAG_BULK) {
                 static_for<Q>([&](auto ic) {
                     constexpr int i = decltype(ic)::value;
-                    fn[i] = St<S>::ld(st, i * BOX + own_b - L::c(i, 1) * BW - L::c(i, 0), L::w(i));
+                    fn[i] = St<S>::ld(st, i * BOX + own_b - L::c(i, 1) * BW - L::c(i, 0), g.shift[i]);
                 });
                 reg_moments<Q, R>(fn, r, u);
             } else if (tn >= 0) {
@@ -1614,7 +1626,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
                     R m0 = R(0), m1 = R(0), m2 = R(0), m3 = R(0);
                     static_for<Q>([&](auto ic) {
                         constexpr int i = decltype(ic)::value;
-                        const R v = St<S>::ld(st, i * BOX + halo_b - L::c(i, 1) * BW - L::c(i, 0), L::w(i));
+                        const R v = St<S>::ld(st, i * BOX + halo_b - L::c(i, 1) * BW - L::c(i, 0), g.shift[i]);
                         m0 += v;
                         if constexpr (L::c(i, 0) > 0) m1 += v;
                         else if constexpr (L::c(i, 0) < 0) m1 -= v;
@@ -1706,7 +1718,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
             hrr_collide<Q, R>(fc, rho, uc, Sv, Cv, tau, om, sigma, spsi);
             static_for<Q>([&](auto ic) {
                 constexpr int i = decltype(ic)::value;
-                St<S>::st(fdst + (long long)i * g.pitch, idx, fc[i], L::w(i));
+                St<S>::st(fdst + (long long)i * g.pitch, idx, fc[i], g.shift[i]);
             });
         }
 #pragma unroll
@@ -1929,7 +1941,7 @@ __global__ void k_probe(ProbeDev P, const LevelDev *__restrict__ levs, const lon
     for (int c = 0; c < (L::D == 3 ? 8 : 4); c++) {
         const int idx = P.node[j * 8 + c];
         double r = 0.0;
-        for (int i = 0; i < Q; i++) r += (double)St<S>::ld(f + (long long)i * Lv.g.pitch, idx, L::w(i));
+        for (int i = 0; i < Q; i++) r += (double)St<S>::ld(f + (long long)i * Lv.g.pitch, idx, Lv.g.shift[i]);
         acc += P.w[j * 8 + c] * r;
     }
     P.samples[(long long)row * P.n + j] = acc;
@@ -1947,10 +1959,11 @@ __global__ void k_init(LevelGeo g, const int *__restrict__ tag, const double *__
     const bool hole = tag[sl] == TAG_HOLE;
     double uu[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < D; a++) uu[a] = u[(long long)a * g.N + idx];
+#pragma unroll
     for (int i = 0; i < Q; i++) {
         const double v = hole ? L::w(i) : feq_one<Q>(i, rho[idx], uu);
-        St<S>::st(f0, (long long)i * g.pitch + sl, (typename St<S>::R)v, L::w(i));
-        St<S>::st(f1, (long long)i * g.pitch + sl, (typename St<S>::R)v, L::w(i));
+        St<S>::st(f0, (long long)i * g.pitch + sl, (typename St<S>::R)v, g.shift[i]);
+        St<S>::st(f1, (long long)i * g.pitch + sl, (typename St<S>::R)v, g.shift[i]);
     }
 }
 
@@ -1965,8 +1978,9 @@ __global__ void k_macros(LevelGeo g, const int *__restrict__ tag, const S *__res
     const long long sl = dense_to_slot(g, idx);
     const bool hole = tag[sl] == TAG_HOLE;
     double r = 0.0, m[3] = {0.0, 0.0, 0.0};
+#pragma unroll
     for (int i = 0; i < Q; i++) {
-        const double v = hole ? 0.0 : (double)St<S>::ld(f, (long long)i * g.pitch + sl, L::w(i));
+        const double v = hole ? 0.0 : (double)St<S>::ld(f, (long long)i * g.pitch + sl, g.shift[i]);
         if (pops) pops[(long long)i * g.N + idx] = v;
         r += v;
         for (int a = 0; a < D; a++) m[a] += L::c(i, a) * v;
@@ -1991,8 +2005,9 @@ __global__ void k_reduce_partial(LevelGeo g, const int *__restrict__ tag, const 
         const long long sl = dense_to_slot(g, idx);
         if (tag[sl] == TAG_HOLE) continue;
         const double w = wnode[idx];
+#pragma unroll
         for (int i = 0; i < Q; i++) {
-            const double v = (double)St<S>::ld(f, (long long)i * g.pitch + sl, L::w(i));
+            const double v = (double)St<S>::ld(f, (long long)i * g.pitch + sl, g.shift[i]);
             if (!isfinite(v)) bad = true;
             acc[0] += w * v;
             for (int a = 0; a < D; a++) acc[1 + a] += w * L::c(i, a) * v;

@@ -49,6 +49,7 @@ class lbm_hierarchy_desc(C.Structure):
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
         ("alloc_ctx", C.c_void_p),
+        ("u_shift", C.c_double * 3),
     ]
 
 
@@ -132,6 +133,9 @@ def make_desc(desc: dict, use_graphs: bool = True) -> lbm_hierarchy_desc:
     d.storage = STORAGE[desc.get("storage", "f64")]
     d.psi_sign = int(desc.get("psi_sign", -1))
     d.use_graphs = int(bool(use_graphs))
+    us = list(desc.get("u_shift", (0.0, 0.0, 0.0))) + [0.0] * 3
+    for a in range(3):
+        d.u_shift[a] = float(us[a])
     return d
 
 

@@ -51,7 +51,8 @@ def test_desc_struct_layout_matches_header(L):
     assert d.box_hi.offset == 32 + 96
     assert d.nu0.offset == 32 + 192
     assert d.alloc.offset % 8 == 0
-    assert C.sizeof(d) == d.alloc_ctx.offset + 8
+    assert d.u_shift.offset == d.alloc_ctx.offset + 8
+    assert C.sizeof(d) == d.u_shift.offset + 24
 
 
 @pytest.mark.parametrize("bad,match", [
