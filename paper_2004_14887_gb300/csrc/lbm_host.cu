@@ -80,6 +80,10 @@ struct lbm_hierarchy {
     // level's sub-steps (fork and join events per level; captured as graph branches)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork[LBM_MAX_LEVELS] = {}, ev_join[LBM_MAX_LEVELS] = {};
+    // third stream: a level's bulk launch starts once its child's sync sub-step has
+    // written this level's child-TF rows (ev_parent) and runs beside the child's rest
+    cudaStream_t side2 = nullptr;
+    cudaEvent_t ev_parent[LBM_MAX_LEVELS] = {}, ev_bulk[LBM_MAX_LEVELS] = {};
     std::vector<DevBuf> bufs;
     int64_t device_bytes = 0;
     int *d_status = nullptr, *d_maxit = nullptr;
@@ -895,24 +899,24 @@ LevelDev level_dev(const lbm_h h, int l)
 // ------------------------------------------------------------------ schedule
 template <int Q, typename S, int TX, int TYT, int NR>
 void launch_bulk2d_cfg(lbm_h h, int l, const void *src, void *dst, typename St<S>::R tau, typename St<S>::R om,
-                       typename St<S>::R sig, typename St<S>::R sps)
+                       typename St<S>::R sig, typename St<S>::R sps, cudaStream_t st)
 {
     const Level &v = h->lev[l];
     const dim3 grid((unsigned)((v.n[0] + TX - 1) / TX), (unsigned)((v.n[1] + TYT * NR - 1) / (TYT * NR)), 1);
-    k_bulk2d<Q, S, TX, TYT, NR><<<grid, TX * TYT, 0, h->stream>>>(level_dev(h, l), (const S *)src, (S *)dst, tau, om,
-                                                                 sig, sps);
+    k_bulk2d<Q, S, TX, TYT, NR><<<grid, TX * TYT, 0, st>>>(level_dev(h, l), (const S *)src, (S *)dst, tau, om, sig,
+                                                          sps);
 }
 
 template <int Q, typename S>
 void launch_bulk2d(lbm_h h, int l, int cfg, const void *src, void *dst, typename St<S>::R tau,
-                   typename St<S>::R om, typename St<S>::R sig, typename St<S>::R sps)
+                   typename St<S>::R om, typename St<S>::R sig, typename St<S>::R sps, cudaStream_t st)
 {
     switch (cfg) {
-    case 1: launch_bulk2d_cfg<Q, S, 32, 4, 4>(h, l, src, dst, tau, om, sig, sps); break;
-    case 2: launch_bulk2d_cfg<Q, S, 32, 8, 1>(h, l, src, dst, tau, om, sig, sps); break;
-    case 3: launch_bulk2d_cfg<Q, S, 64, 4, 2>(h, l, src, dst, tau, om, sig, sps); break;
-    case 4: launch_bulk2d_cfg<Q, S, 32, 16, 1>(h, l, src, dst, tau, om, sig, sps); break;
-    default: launch_bulk2d_cfg<Q, S, 32, 8, 2>(h, l, src, dst, tau, om, sig, sps); break;
+    case 1: launch_bulk2d_cfg<Q, S, 32, 4, 4>(h, l, src, dst, tau, om, sig, sps, st); break;
+    case 2: launch_bulk2d_cfg<Q, S, 32, 8, 1>(h, l, src, dst, tau, om, sig, sps, st); break;
+    case 3: launch_bulk2d_cfg<Q, S, 64, 4, 2>(h, l, src, dst, tau, om, sig, sps, st); break;
+    case 4: launch_bulk2d_cfg<Q, S, 32, 16, 1>(h, l, src, dst, tau, om, sig, sps, st); break;
+    default: launch_bulk2d_cfg<Q, S, 32, 8, 2>(h, l, src, dst, tau, om, sig, sps, st); break;
     }
 }
 
@@ -926,8 +930,9 @@ bool node_mapping(const lbm_h h, int n)
 
 template <int Q, typename S>
 struct Sched {
-    static void bulk(lbm_h h, int l, const void *src, void *dst)
+    static void bulk(lbm_h h, int l, const void *src, void *dst, cudaStream_t stream = nullptr)
     {
+        const cudaStream_t st = stream ? stream : h->stream;
         const Level &v = h->lev[l];
         const dim3 nt(v.tiles[0], v.tiles[1], v.tiles[2]);
         const double spsi = (double)h->d.psi_sign;
@@ -944,9 +949,9 @@ struct Sched {
         using R = typename St<S>::R;
         const R tau = (R)v.tau, om = (R)(1.0 - 1.0 / v.tau), sig = (R)h->d.sigma, sps = (R)spsi;
         if constexpr (Lat<Q>::D == 2)
-            launch_bulk2d<Q, S>(h, l, v.tile_cfg, src, dst, tau, om, sig, sps);
+            launch_bulk2d<Q, S>(h, l, v.tile_cfg, src, dst, tau, om, sig, sps, st);
         else
-            k_bulk3d<Q, S, T3X, T3Y><<<nt, T3X * T3Y, Stage3<Q, S, T3X, T3Y>::smem_bytes, h->stream>>>(
+            k_bulk3d<Q, S, T3X, T3Y><<<nt, T3X * T3Y, Stage3<Q, S, T3X, T3Y>::smem_bytes, st>>>(
                 v.tmap[src == v.f[0] ? 0 : 1], level_dev(h, l), (const S *)src, (S *)dst, tau, om, sig, sps, v.zc,
                 h->d_status, kWaitLimitNs);
         h->launch_counter++;
@@ -1020,12 +1025,25 @@ struct Sched {
                 if (forked) cudaEventRecord(h->ev_join[l], h->side);
             }
         }
+        // a sync sub-step has now issued everything that writes the parent's child-TF
+        // rows (the coarse rebuild in the Newton launch, S and C in the gradient launch)
+        if (l > 0 && phase == 1) cudaEventRecord(h->ev_parent[l], forked ? h->side : h->stream);
         if (l + 1 < h->nl) {
             level_step(h, l + 1, 2 * k, 0, k);
             level_step(h, l + 1, 2 * k + 1, 1, k);
         }
-        if (forked) cudaStreamWaitEvent(h->stream, h->ev_join[l], 0);
-        bulk(h, l, fA, fB);
+        if (l + 1 < h->nl && !h->timing) {
+            // this level's bulk launch beside the rest of the child's sync sub-step; the
+            // main stream joins it before anything can read this level's new state
+            cudaStreamWaitEvent(h->side2, h->ev_parent[l + 1], 0);
+            if (forked) cudaStreamWaitEvent(h->side2, h->ev_join[l], 0);
+            bulk(h, l, fA, fB, h->side2);
+            cudaEventRecord(h->ev_bulk[l], h->side2);
+            cudaStreamWaitEvent(h->stream, h->ev_bulk[l], 0);
+        } else {
+            if (forked) cudaStreamWaitEvent(h->stream, h->ev_join[l], 0);
+            bulk(h, l, fA, fB);
+        }
     }
 
     static void coarse_step(lbm_h h, long long n) { level_step(h, 0, n, 1, -1); }
@@ -1189,10 +1207,13 @@ int lbm_create_hierarchy(const lbm_hierarchy_desc *desc, void *cuda_stream, lbm_
         }
         h->own_stream = true;
     }
-    bool evok = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) == cudaSuccess;
+    bool evok = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) == cudaSuccess &&
+                cudaStreamCreateWithFlags(&h->side2, cudaStreamNonBlocking) == cudaSuccess;
     for (int l = 0; l < LBM_MAX_LEVELS && evok; l++)
         evok = cudaEventCreateWithFlags(&h->ev_fork[l], cudaEventDisableTiming) == cudaSuccess &&
-               cudaEventCreateWithFlags(&h->ev_join[l], cudaEventDisableTiming) == cudaSuccess;
+               cudaEventCreateWithFlags(&h->ev_join[l], cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&h->ev_parent[l], cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&h->ev_bulk[l], cudaEventDisableTiming) == cudaSuccess;
     if (!evok) {
         g_create_error = "cudaStreamCreateWithFlags / cudaEventCreateWithFlags failed";
         lbm_destroy(h);
@@ -1429,14 +1450,14 @@ void lbm_destroy(lbm_h h)
         if (h->d.free) h->d.free(b.p, h->d.alloc_ctx);
         else cudaFree(b.p);
     }
-    if (h->side) {
-        cudaStreamSynchronize(h->side);
-        cudaStreamDestroy(h->side);
-    }
-    for (int l = 0; l < LBM_MAX_LEVELS; l++) {
-        if (h->ev_fork[l]) cudaEventDestroy(h->ev_fork[l]);
-        if (h->ev_join[l]) cudaEventDestroy(h->ev_join[l]);
-    }
+    for (cudaStream_t s2 : {h->side, h->side2})
+        if (s2) {
+            cudaStreamSynchronize(s2);
+            cudaStreamDestroy(s2);
+        }
+    for (int l = 0; l < LBM_MAX_LEVELS; l++)
+        for (cudaEvent_t e : {h->ev_fork[l], h->ev_join[l], h->ev_parent[l], h->ev_bulk[l]})
+            if (e) cudaEventDestroy(e);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
