@@ -1376,13 +1376,19 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
     return true;
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// element copy global -> shared without the register file (4 or 8 bytes; zero-fill when !ok)
+// copy global -> shared without the register file (4, 8 or 16 bytes, both addresses
+// aligned to the size; zero-fill when !ok)
 template <int B>
 __device__ __forceinline__ void cp_async(void *dst, const void *src, bool ok)
 {
-    static_assert(B == 4 || B == 8, "cp.async element size");
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(saddr(dst)), "l"(src), "n"(B), "r"(ok ? B : 0)
-                 : "memory");
+    static_assert(B == 4 || B == 8 || B == 16, "cp.async size");
+    if constexpr (B == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr(dst)), "l"(src), "r"(ok ? 16 : 0)
+                     : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(saddr(dst)), "l"(src), "n"(B),
+                     "r"(ok ? B : 0)
+                     : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
@@ -1482,6 +1488,10 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
     // a column whose stage would cross a periodic seam in x or y is filled by plain loads
     const bool seam = (g.per[0] && (X0 - 2 < 0 || X0 + TX + 1 > g.n[0] - 1)) ||
                       (g.per[1] && (Y0 - 2 < 0 || Y0 + TY + 1 > g.n[1] - 1));
+    // seam stages in 16-byte chunks when a periodic x extent is whole chunks, else by
+    // elements; both asynchronous except element copies of 2-byte storage
+    const bool chunked = !g.per[0] || g.n[0] % (16 / (int)sizeof(S)) == 0;
+    const bool async_fill = chunked || sizeof(S) >= 4;
 
     // seam columns: the box elements a thread copies are the same in every plane;
     // their wrapped x-y slot offsets (-1: off a non-periodic box) are fixed here
@@ -1526,9 +1536,38 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
                 });
             }
             pending |= 1u << s;
+        } else if (chunked) {
+            // 16-byte asynchronous copies with wrapped coordinates: a box row is whole
+            // 16-byte chunks, and with a periodic x extent of whole chunks a chunk never
+            // straddles the seam (completed before the barrier that precedes the use)
+            int zo[3];  // slot offset of planes p+1, p, p-1 (c_z = -1, 0, 1); -1 off the box
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                int sz = p + 1 - c;
+                zo[c] = wrap_coord(sz, g.n[2], g.per[2]) ? n01 * sz : -1;
+            }
+            constexpr int CE = 16 / (int)sizeof(S), CPR = BW / CE, NCH = CPR * G::BH;
+            static_assert(BW % CE == 0 && NCH <= NT, "one chunk per thread and population");
+            if (tid < NCH) {
+                const int row = tid / CPR, cc = tid % CPR;
+                int sx = X0 - XA + cc * CE, sy = Y0 - 2 + row;
+                // off a non-periodic x extent: a chunk that starts inside the row ends
+                // inside its padded pitch (px is a multiple of 8 nodes)
+                const bool okxy = wrap_coord(sy, g.n[1], g.per[1]) &&
+                                  (g.per[0] ? wrap_coord(sx, g.n[0], 1) : (sx >= 0 && sx < g.n[0]));
+                const int oxy = okxy ? sx + g.px * sy : 0;
+                static_for<Q>([&](auto ic) {
+                    constexpr int i = decltype(ic)::value;
+                    const int z0 = zo[L::c(i, 2) + 1];
+                    const bool ok = okxy && z0 >= 0;
+                    tma::cp_async<16>(dst + i * BOX + row * BW + cc * CE,
+                                      fsrc + (long long)i * g.pitch + (ok ? oxy + z0 : 0), ok);
+                });
+            }
+            tma::cp_async_commit();
         } else {
-            // plain copies with wrapped coordinates (asynchronous for 4- and 8-byte types;
-            // completed before the barrier that precedes the stage's use)
+            // element copies with wrapped coordinates (asynchronous for 4- and 8-byte
+            // types; completed before the barrier that precedes the stage's use)
             int zo[3];  // slot offset of planes p+1, p, p-1 (c_z = -1, 0, 1); -1 off the box
 #pragma unroll
             for (int c = 0; c < 3; c++) {
@@ -1576,8 +1615,8 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
     int c0 = class_of(0), c1 = class_of(1);  // classes of planes k, k + 1 (K >= 3)
     issue(0, c0);
     issue(1, c1);
-    if (seam) {  // stages filled by plain copies
-        if constexpr (sizeof(S) >= 4) tma::cp_async_wait_all();
+    if (seam) {  // stages filled by copies from the threads
+        if (async_fill) tma::cp_async_wait_all();
         __syncthreads();
     }
     if (c0 == LOAD_GENERAL) tags_of(0, nt_own, nt_halo);
@@ -1652,8 +1691,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
             for (int a = 0; a < D; a++) s_u[(slot * 3 + a) * HP + hb] = hu[a];
         }
         if (!in_xy) tn = TAG_HOLE;  // a position past a periodic seam only feeds the halo
-        if constexpr (sizeof(S) >= 4)
-            if (seam) tma::cp_async_wait_all();  // the copies of the next stage, issued one plane ago
+        if (seam && async_fill) tma::cp_async_wait_all();  // the copies of the next stage, issued one plane ago
         if (__syncthreads_or(!ok)) {
             // a copy did not arrive in time: report, drain what is in flight, stop
             if (tid == 0) atomicOr(status, ST_TIMEOUT);

@@ -380,3 +380,18 @@ def test_f16_storage_shifted_by_mean_flow_equilibrium():
         errs[shift] = _assert_parity(g, o, 3e-3)
     worst = {k: max(max(er, eu) for er, eu, _ in v) for k, v in errs.items()}
     assert worst[True] < 0.5 * worst[False], worst
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 5e-5), ("f16s", 3e-3)])
+def test_d3q19_periodic_extent_not_whole_chunks(storage, tol):
+    """Level 0 of 34 x 20 x 16 nodes: its periodic x extent is not a whole number of
+    16-byte chunks in FP32 and FP16, so seam columns fill their stage element by
+    element; in FP64 (two nodes per chunk) they take 16-byte chunks."""
+    d = {"lattice": 19, "coarse_n": (34, 20, 16), "boxes": [((8, 4, 4), (24, 16, 12))], "nu0": 1e-5,
+         "storage": storage,
+         "init": {"kind": "pulse+vortex", "xc": 15.3, "yc": 9.6, "zc": 7.4, "Rc": 1.5, "A": 1e-3,
+                  "swirl": 0.05, "U": (0.05, 0.02, 0.01), "noise": 0.01, "seed": 9}}
+    g, o = _pair(d)
+    g.advance(4)
+    o.advance(4)
+    _assert_parity(g, o, tol)
