@@ -897,14 +897,32 @@ LevelDev level_dev(const lbm_h h, int l)
 }
 
 // ------------------------------------------------------------------ schedule
+// a launch that may start while the previous kernel of its stream finishes (the
+// kernel waits for that kernel's completion before touching memory: pdl_enter)
+template <typename... KArgs, typename... Args>
+void launch_chained(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 template <int Q, typename S, int TX, int TYT, int NR>
 void launch_bulk2d_cfg(lbm_h h, int l, const void *src, void *dst, typename St<S>::R tau, typename St<S>::R om,
                        typename St<S>::R sig, typename St<S>::R sps, cudaStream_t st)
 {
     const Level &v = h->lev[l];
     const dim3 grid((unsigned)((v.n[0] + TX - 1) / TX), (unsigned)((v.n[1] + TYT * NR - 1) / (TYT * NR)), 1);
-    k_bulk2d<Q, S, TX, TYT, NR><<<grid, TX * TYT, 0, st>>>(level_dev(h, l), (const S *)src, (S *)dst, tau, om, sig,
-                                                          sps);
+    launch_chained(k_bulk2d<Q, S, TX, TYT, NR>, grid, dim3(TX * TYT), 0, st, level_dev(h, l), (const S *)src, (S *)dst,
+                   tau, om, sig, sps);
 }
 
 template <int Q, typename S>
@@ -951,9 +969,9 @@ struct Sched {
         if constexpr (Lat<Q>::D == 2)
             launch_bulk2d<Q, S>(h, l, v.tile_cfg, src, dst, tau, om, sig, sps, st);
         else
-            k_bulk3d<Q, S, T3X, T3Y><<<nt, T3X * T3Y, Stage3<Q, S, T3X, T3Y>::smem_bytes, st>>>(
-                v.tmap[src == v.f[0] ? 0 : 1], level_dev(h, l), (const S *)src, (S *)dst, tau, om, sig, sps, v.zc,
-                h->d_status, kWaitLimitNs);
+            launch_chained(k_bulk3d<Q, S, T3X, T3Y>, nt, dim3(T3X * T3Y), Stage3<Q, S, T3X, T3Y>::smem_bytes, st,
+                           v.tmap[src == v.f[0] ? 0 : 1], level_dev(h, l), (const S *)src, (S *)dst, tau, om, sig,
+                           sps, v.zc, h->d_status, kWaitLimitNs);
         h->launch_counter++;
         if (h->timing) {
             cudaEventRecord(h->ev_pool[ev + 1], h->stream);
@@ -987,14 +1005,9 @@ struct Sched {
             const int per = per_block(nr + nh);
             const int nbr = (nr + per - 1) / per, nbh = (nh + per - 1) / per;
             const LevelDev dc = l > 0 ? level_dev(h, l - 1) : dv;
-            if (per == 128)
-                k_recon_hist<Q, S, true><<<nbr + nbh, 128, 0, h->stream>>>(Ir, dv, dc, (const S *)fA, tw, phase,
-                                                                           h->d_status, h->d_maxit, nbr, Ih, dv.g,
-                                                                           (const S *)fA, (int)((k + 1) % 3));
-            else
-                k_recon_hist<Q, S, false><<<nbr + nbh, 128, 0, h->stream>>>(Ir, dv, dc, (const S *)fA, tw, phase,
-                                                                            h->d_status, h->d_maxit, nbr, Ih, dv.g,
-                                                                            (const S *)fA, (int)((k + 1) % 3));
+            launch_chained(per == 128 ? k_recon_hist<Q, S, true> : k_recon_hist<Q, S, false>, dim3(nbr + nbh), dim3(128),
+                           0, h->stream, Ir, dv, dc, (const S *)fA, tw, phase, h->d_status, h->d_maxit, nbr, Ih, dv.g,
+                           (const S *)fA, (int)((k + 1) % 3));
             h->launch_counter++;
         }
         // TF gradients and hanging nodes of this level read this level's populations, TF
@@ -1015,12 +1028,8 @@ struct Sched {
                     st = h->side;
                     forked = true;
                 }
-                if (per == 128)
-                    k_grad_ie<Q, S, true><<<nbg + nbi, 128, 0, st>>>(I, dv, level_dev(h, l - 1), (const S *)fA, tw,
-                                                                     phase, nbg);
-                else
-                    k_grad_ie<Q, S, false><<<nbg + nbi, 128, 0, st>>>(I, dv, level_dev(h, l - 1), (const S *)fA, tw,
-                                                                      phase, nbg);
+                launch_chained(per == 128 ? k_grad_ie<Q, S, true> : k_grad_ie<Q, S, false>, dim3(nbg + nbi), dim3(128), 0,
+                               st, I, dv, level_dev(h, l - 1), (const S *)fA, tw, phase, nbg);
                 h->launch_counter++;
                 if (forked) cudaEventRecord(h->ev_join[l], h->side);
             }

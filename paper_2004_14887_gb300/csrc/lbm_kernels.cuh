@@ -983,6 +983,17 @@ __device__ __forceinline__ void ie_node(int bid, IfaceDev I, LevelDev F, const S
     for (int a = 0; a < 3; a++) fmac[(long long)(1 + a) * nif + row] = a < D ? m[a] / rho : R(0);
 }
 
+// ------------------------------------------------------------------ launch chaining
+// Programmatic dependent launch: the schedule's kernels first wait until the previous
+// kernel of their stream has completed and flushed its memory (a no-op for a launch
+// without the attribute), then allow the next kernel to start launching, so that its
+// launch and block scheduling overlap this kernel's run.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ------------------------------------------------------------------ fused launches
 // blocks [0, nb_a) run the first body, the rest the second: the two halves work on
 // independent data (a different interface, or TF nodes vs hanging nodes of the same
@@ -993,6 +1004,7 @@ __global__ void __launch_bounds__(128) k_recon_hist(IfaceDev Ir, LevelDev F, Lev
                                                       TimeW tw, int sync, int *status, int *max_iters, int nb_recon,
                                                       IfaceDev Ih, LevelGeo gh, const S *__restrict__ fh, int slot)
 {
+    pdl_enter();
     if ((int)blockIdx.x < nb_recon) {
         if constexpr (NODE) recon_node<Q, S>(blockIdx.x, Ir, F, Cl, ff, tw, sync, status, max_iters);
         else recon_seg<Q, S>(blockIdx.x, Ir, F, Cl, ff, tw, sync, status, max_iters);
@@ -1012,6 +1024,7 @@ template <int Q, typename S, bool NODE>
 __global__ void __launch_bounds__(128) k_grad_ie(IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict__ ff,
                                                    TimeW tw, int sync, int nb_grad)
 {
+    pdl_enter();
     if ((int)blockIdx.x < nb_grad) {
         if constexpr (NODE) grad_node<Q, S>(blockIdx.x, I, F, Cl, ff, tw, sync);
         else grad_seg<Q, S>(blockIdx.x, I, F, Cl, ff, tw, sync);
@@ -1302,6 +1315,7 @@ __global__ void __launch_bounds__(TX *TYT, sizeof(S) == 8 ? 1 : (TX * TYT >= 256
                                                      typename St<S>::R tau, typename St<S>::R om,
                                                      typename St<S>::R sigma, typename St<S>::R spsi)
 {
+    pdl_enter();
     bulk2d_tile<Q, S, TX, TYT, NR>(Lv, fsrc, fdst, tau, om, sigma, spsi, blockIdx.x, blockIdx.y);
 }
 
@@ -1437,6 +1451,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
              typename St<S>::R tau, typename St<S>::R om, typename St<S>::R sigma, typename St<S>::R spsi, int zc,
              int *status, unsigned long long limit_ns)
 {
+    pdl_enter();
     using L = Lat<Q>;
     using G = Stage3<Q, S, TX, TY>;
     using R = typename St<S>::R;
