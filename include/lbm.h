@@ -23,7 +23,9 @@
  *   (the Python binding backs them with PyTorch's caching allocator), else
  *   through cudaMalloc/cudaFree, and released by lbm_destroy.
  * - All device work is issued on the stream given at creation (a private
- *   non-blocking stream when NULL) and is stream-ordered.
+ *   non-blocking stream when NULL) and is stream-ordered.  lbm_advance forks part of
+ *   a coarse step onto two internal streams of the handle and joins them back into
+ *   that stream before the step ends.
  */
 #ifndef LBM_GB300_H
 #define LBM_GB300_H
@@ -186,8 +188,8 @@ LBM_API int lbm_get_probes(lbm_h h, double *out, int64_t *n_samples);
  * interface histories of Eq. (TempInt) and the step counter) as one host buffer.
  * lbm_save_state with buf == NULL returns the size in *len; lbm_load_state restores
  * a state saved from a hierarchy of the same description (checked: lattice, storage,
- * levels, box sizes), after which lbm_advance continues bit for bit as the saved run
- * would have.  Both synchronise the stream. */
+ * FP16 shift, levels, box sizes), after which lbm_advance continues bit for bit as the
+ * saved run would have.  Both synchronise the stream. */
 LBM_API int lbm_save_state(lbm_h h, void *buf, size_t *len);
 LBM_API int lbm_load_state(lbm_h h, const void *buf, size_t len);
 

@@ -1867,6 +1867,16 @@ static size_t state_bytes(const lbm_h h)
     return b;
 }
 
+// 64-bit FNV-1a of the FP16 storage shift, so that a state is loaded only where its
+// stored populations mean the same values
+static uint64_t shift_key(const lbm_h h)
+{
+    uint64_t k = 1469598103934665603ull;
+    const unsigned char *b = (const unsigned char *)h->shift;
+    for (size_t i = 0; i < sizeof(h->shift); i++) k = (k ^ b[i]) * 1099511628211ull;
+    return k;
+}
+
 int lbm_save_state(lbm_h h, void *buf, size_t *len)
 {
     if (!h || !len) return h ? fail(h, LBM_ERR_ARG, "len is NULL") : LBM_ERR_ARG;
@@ -1885,7 +1895,7 @@ int lbm_save_state(lbm_h h, void *buf, size_t *len)
     hd[3] = (uint64_t)h->d.storage;
     hd[4] = (uint64_t)h->nl;
     hd[5] = (uint64_t)h->ncoarse;
-    hd[6] = 0;
+    hd[6] = shift_key(h);
     hd[7] = 0;
     for (int l = 0; l < LBM_MAX_LEVELS; l++) hd[8 + l] = l < h->nl ? (uint64_t)h->lev[l].N : 0;
     char *p = (char *)buf + 8 * 8 + 8 * LBM_MAX_LEVELS;
@@ -1915,8 +1925,8 @@ int lbm_load_state(lbm_h h, const void *buf, size_t len)
     const size_t need = state_bytes(h);
     const uint64_t *hd = (const uint64_t *)buf;
     if (len < need || hd[0] != kStateMagic || hd[1] != 1 || hd[2] != (uint64_t)h->Q ||
-        hd[3] != (uint64_t)h->d.storage || hd[4] != (uint64_t)h->nl)
-        return fail(h, LBM_ERR_ARG, "state does not belong to this hierarchy (lattice, storage, levels or size)");
+        hd[3] != (uint64_t)h->d.storage || hd[4] != (uint64_t)h->nl || hd[6] != shift_key(h))
+        return fail(h, LBM_ERR_ARG, "state does not belong to this hierarchy (lattice, storage, shift, levels or size)");
     for (int l = 0; l < h->nl; l++)
         if (hd[8 + l] != (uint64_t)h->lev[l].N) return fail(h, LBM_ERR_ARG, "level %d has another box", l);
     CK(cudaStreamSynchronize(h->stream));
