@@ -62,6 +62,8 @@ def test_desc_struct_layout_matches_header(L):
     ({"boxes": [((8, 8), (24, 24)), ((9, 9), (20, 20))]}, "margin"),
     ({"nu0": -1.0}, "nu0"),
     ({"dc_variant": 3}, "dc_variant"),
+    ({"storage": "f16s", "u_shift": (0.5, 0.0, 0.0)}, "u_shift"),
+    ({"storage": "f16s", "u_shift": (0.05, 0.0, 0.01)}, "u_shift"),
 ])
 def test_malformed_descriptions_are_rejected_on_the_host(L, bad, match):
     desc = {"lattice": 9, "coarse_n": (32, 32), "boxes": [((8, 8), (24, 24))], "nu0": 1e-5}
