@@ -5,6 +5,7 @@
 // declared in include/lbm.h.
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>  // header-only; the markers cost nothing without a profiler
 
 #include <algorithm>
 #include <cmath>
@@ -24,6 +25,15 @@ using namespace lbmg;
 namespace {
 
 thread_local std::string g_create_error;
+
+// NVTX range for profiler timelines (lbm_advance, coarse steps, level sub-steps)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+const char *const kLevelRange[LBM_MAX_LEVELS] = {"level 0 step", "level 1 step", "level 2 step", "level 3 step"};
 
 struct DevBuf {
     void *p = nullptr;
@@ -984,6 +994,7 @@ struct Sched {
     // one step of level l (Sec. 3.5): k is the level's step index, kp its parent's
     static void level_step(lbm_h h, int l, long long k, int phase, long long kp)
     {
+        NvtxRange range(kLevelRange[l]);
         Level &v = h->lev[l];
         const void *fA = v.f[k & 1];
         void *fB = v.f[(k + 1) & 1];
@@ -1311,8 +1322,10 @@ int lbm_advance(lbm_h h, int64_t n)
     if (!h) return LBM_ERR_ARG;
     if (n < 0) return fail(h, LBM_ERR_ARG, "negative step count");
     if (h->batch) return fail(h, LBM_ERR_ARG, "this hierarchy belongs to a batch: advance the batch");
+    NvtxRange range("lbm_advance");
     if (!h->members.empty()) return batch_advance(h, n);
     for (int64_t s = 0; s < n; s++) {
+        NvtxRange step("coarse step");
         const long long k = h->ncoarse;
         int rc;
         if (h->d.use_graphs && !h->timing && k >= 1) rc = run_graph(h, k);
