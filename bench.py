@@ -163,6 +163,21 @@ def _workloads():
             "batch2d": W.batch2d}
 
 
+def kernel_source_key(csrc):
+    """Hash of the device code (kernel and device headers) with comments and blank
+    lines removed: a traffic figure measured by ncu stays valid while the code is
+    unchanged."""
+    import hashlib
+
+    h = hashlib.sha1()
+    for name in ("lbm_kernels.cuh", "lbm_device.cuh"):
+        txt = open(os.path.join(csrc, name)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        txt = re.sub(r"//[^\n]*", "", txt)
+        h.update("\n".join(ln.rstrip() for ln in txt.splitlines() if ln.strip()).encode())
+    return h.hexdigest()[:12]
+
+
 def _traffic_from_profiles(workload, storage):
     """DRAM bytes per launch recorded by an ncu capture in profiles/ for this kernel,
     workload and kernel-source revision, or None."""
@@ -174,10 +189,7 @@ def _traffic_from_profiles(workload, storage):
 
         import hashlib
 
-        h = hashlib.sha1()
-        for s in [os.path.join(B.CSRC, "lbm_kernels.cuh"), os.path.join(B.CSRC, "lbm_device.cuh")]:
-            h.update(open(s, "rb").read())
-        sha = h.hexdigest()[:12]
+        sha = kernel_source_key(B.CSRC)
         txt = open(path).read()
         m = re.search(r"traffic_per_full_launch_bytes:\s*([0-9.eE+]+)\s+source_sha:\s*(\w+)", txt)
         if m and m.group(2) == sha:

@@ -1,17 +1,19 @@
 // Device code of the GB300 direct-coupling multi-level lattice Boltzmann library.
 //
 // Hot path per level sub-step (Sec. 3.5 of Astoul et al., arXiv 2004.14887):
-//   k_hist   coarse post-stream populations at TF nodes and macros on the ring of
-//            coarse stencil nodes -> 3-slot history (for Eq. TempInt)
-//   k_recon  Newton at TF nodes (Eqs. system_fi, updated_macro), fine rebuild of the
-//            gamma=c populations (Eq. rescff) and, on sync sub-steps, coarse rebuild of
-//            every population (Eq. rescfc) -- FP64
-//   k_grad   coarse-stencil S and C = div Psi at TF nodes (Sec. 3.3), x1/2 for the fine
-//            level (Eqs. PijResc, PSIResc) -- FP64
-//   k_ie     4-point 1-D Lagrange of missing populations, S and C at hanging nodes -- FP64
-//   k_bulk   fused pull-stream + moments (tile + 1 halo in shared memory) + centred
-//            finite differences (Eqs. a1FD_scheme, PSI_FD) + H-RR collision
-//            (Eqs. fEq_herm, a12_HRR, a1Proj, a13RR, LBMscheme_reg, App. A) + store
+//   k_recon_hist  Newton at TF nodes (Eqs. system_fi, updated_macro) in the arithmetic
+//                 type, fine rebuild of the gamma=c populations (Eq. rescff) and, on
+//                 sync sub-steps, coarse rebuild of every population (Eq. rescfc) in
+//                 FP64; fused with the history push for the child interface (coarse
+//                 post-stream populations at TF nodes and ring macros, Eq. TempInt)
+//   k_grad_ie     coarse-stencil S and C = div Psi at TF nodes (Sec. 3.3), x1/2 for
+//                 the fine level (Eqs. PijResc, PSIResc); fused with the 4-point 1-D
+//                 Lagrange completion of hanging nodes
+//   k_bulk2d / k_bulk3d  fused pull-stream + moments (2-D tile or 3-D z-marching
+//                 column with staged planes, 1-node halo) + centred finite differences
+//                 (Eqs. a1FD_scheme, PSI_FD) + H-RR collision (Eqs. fEq_herm, a12_HRR,
+//                 a1Proj, a13RR, LBMscheme_reg, App. A) + store
+//   k_batch       all of the above for many D2Q9 hierarchies in one persistent launch
 #pragma once
 
 #include <cuda_fp16.h>
