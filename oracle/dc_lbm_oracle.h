@@ -17,7 +17,7 @@
  *   cubic-Mach correction App. A, Eqs. (psi), (Psi), (PSI_FD)
  *   level rescaling       Sec. 3.1, Eqs. (rescNu), (rescTau), (fneqResc), (PijResc), (PSIResc)
  *   DC interface          Sec. 3.2-3.5, Eqs. (cond_fneq) ... (rescfc), Table 1, App. B
- * Readings of ambiguous passages are listed in the design doc of the repository.
+ * Where the paper is ambiguous, the reading taken is stated at the code that applies it.
  */
 #ifndef DC_LBM_ORACLE_H
 #define DC_LBM_ORACLE_H
