@@ -124,6 +124,18 @@ def test_pulse2d_three_level_full_size_f64():
     _assert_parity(g, o, 1e-12, tol_dev=1e-9)
 
 
+def test_pulse2d_three_level_full_size_f32_bench_configuration():
+    """The bench's default line: the same full-size workload in FP32 storage with the
+    tile shapes the autotuner picks on the live state (as bench.py does), graph
+    replayed, 12 coarse steps against the FP64 oracle (FP32 bound of this module)."""
+    d = W.pulse2d(steps=12, storage="f32")
+    g, o = _pair(d)
+    g.autotune(reps=3)
+    g.advance(12)
+    o.advance(12)
+    _assert_parity(g, o, 5e-5)
+
+
 def test_dc1_variant_f64():
     d = W.vortex2d(n=64, patch=(16, 48), steps=40)
     d["dc_variant"] = 1
