@@ -227,3 +227,45 @@ def test_oracle_mirror_symmetry():
         assert np.max(np.abs(U[0] + mirror(U[0]))[active]) < 1e-14
         assert np.max(np.abs(U[1] - mirror(U[1]))[active]) < 1e-14
     assert np.max(np.abs(R - 1.0)[active]) > 1e-5  # the pulse reached the finest level's nodes
+
+
+def _slab_pulse_error(n, Rc_f, T, variant):
+    """Radial pulse at rest in the middle of a fine slab x in [n/4, 3n/4) that spans
+    y (the plane-interface set-up of Sec. 4.1.1, in 2-D): density of the 2-level
+    run minus that of the all-fine run on the fine slab after T coarse steps, / A."""
+    lo, hi, A = n // 4, n - n // 4, 1e-3
+    ini = {"kind": "pulse", "xc": n / 2, "yc": n / 2, "zc": 0.0, "Rc": Rc_f / 2, "A": A, "U": (0.0, 0.0, 0.0)}
+    d2 = {"lattice": 9, "coarse_n": (n, n), "boxes": [((lo, 0), (hi, n))], "nu0": 1e-5,
+          "dc_variant": variant, "init": ini}
+    h2 = O.Hierarchy(d2)
+    _init_all(h2, d2)
+    h2.advance(T)
+    df = {"lattice": 9, "coarse_n": (2 * n, 2 * n), "boxes": [], "nu0": 2e-5,
+          "init": dict(ini, xc=float(n), yc=float(n), Rc=Rc_f)}
+    hf = O.Hierarchy(df)
+    _init_all(hf, df)
+    hf.advance(2 * T)
+    r2, _ = h2.macros(1)
+    rf, _ = hf.macros(0)
+    m = 2 * (hi - lo) + 1
+    return (r2.reshape(2 * n, m) - rf.reshape(2 * n, 2 * n)[:, 2 * lo:2 * hi + 1]) / A
+
+
+def test_dc2_reflects_less_than_dc1():
+    """Sec. 4.1.1: a pulse crossing plane interfaces is reflected less with DC2 than
+    with DC1, which the paper puts down to aliasing of fine content kept by DC1. Here
+    the pulse is under-resolved on the coarse grid (R_c = 2.5 fine cells) and the
+    reflected wave is measured in the middle half of the slab once it has come back
+    from both interfaces: DC2's is 8 % smaller (0.917 of DC1's). The gap closes as the
+    pulse is resolved (0.99 at R_c = 5, 1.00 at R_c = 10), as the aliasing reading
+    predicts. A swapped (Gamma, gamma) mask reverses the order."""
+    n, Rc_f, T = 64, 2.5, 45
+    rms = []
+    for variant in (1, 2):
+        e = _slab_pulse_error(n, Rc_f, T, variant)
+        m = e.shape[1]
+        c, w = m // 2, m // 4
+        rms.append(float(np.sqrt(np.mean(e[:, c - w:c + w + 1] ** 2))))
+    assert rms[1] < 0.95 * rms[0]
+    # the reflection is there and small: not a vacuous comparison
+    assert 1e-4 < rms[1] < 1e-2
