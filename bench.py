@@ -438,9 +438,10 @@ def run_gb300(args):
         del hs
 
     # end to end through the public API with host buffers: the initial fields from
-    # pinned host memory (H2D), then every step advances and reads the finest level's
-    # mass and momentum back to the host (D2H, lbm_reduce, synchronising), and at the
-    # end the macros of every level (D2H)
+    # pinned host memory (H2D), then every step advances and copies the finest level's
+    # mass and momentum into its row of a pinned host array (D2H, lbm_reduce_async,
+    # stream-ordered), and at the end the macros of every level (D2H, synchronising);
+    # the handle is set up as a user would: created, initialised, autotuned
     e2e = None
     if not args.no_e2e:
         de = _with_storage(WORKLOADS[args.workload](), main_storage)
@@ -451,29 +452,40 @@ def run_gb300(args):
             rp = torch.from_numpy(r).pin_memory().numpy()
             up = torch.from_numpy(u).pin_memory().numpy()
             fields.append((rp, up))
+            he.init_fields(l, rp, up)
+        if not args.no_autotune:
+            he.autotune(reps=10)
         outs = [(torch.empty(he.levels[l]["N"], dtype=torch.float64).pin_memory().numpy(),
                  torch.empty((he.D, he.levels[l]["N"]), dtype=torch.float64).pin_memory().numpy())
                 for l in range(he.n_levels)]
+        sums = torch.zeros((K, 4), dtype=torch.float64).pin_memory()
+        # warm-up on the workload's own state (graph capture); the timed region starts
+        # again from the initial fields
         he.advance(3)
+        he.check_status()
         torch.cuda.synchronize()
         barrier()
         te = time.perf_counter()
         for l in range(he.n_levels):
             he.init_fields(l, *fields[l])
-        for _ in range(K):
+        for k in range(K):
             he.advance(1)
-            he.reduce(he.n_levels - 1)
+            he.reduce_async(he.n_levels - 1, sums[k])
         for l in range(he.n_levels):
             he.get_macros(l, out=outs[l])
         torch.cuda.synchronize()
         barrier()
         tw = max_over_ranks_gpu(time.perf_counter() - te)
+        he.check_status()
+        if not bool(torch.isfinite(sums).all()):
+            raise RuntimeError("end-to-end run: non-finite mass or momentum")
         h2d = sum(a.nbytes + b.nbytes for a, b in fields)
-        d2h = sum(a.nbytes + b.nbytes for a, b in outs) + K * 4 * 8
+        d2h = sum(a.nbytes + b.nbytes for a, b in outs) + sums.numel() * 8
         e2e = {"value": ws * feq * K / tw / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
                "d2h_bytes_per_step": d2h / K,
-               "per_step": "advance one coarse step + FP64 mass/momentum of the finest level to the host; "
-                           "initial fields H2D and final macros D2H amortised over the steps"}
+               "per_step": "advance one coarse step + FP64 mass/momentum of the finest level into a pinned "
+                           "host row (stream-ordered, no per-step synchronisation); initial fields H2D and "
+                           "final macros D2H amortised over the steps; no L2 flush between steps"}
         he.close()
 
     line = {

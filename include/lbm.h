@@ -153,6 +153,20 @@ LBM_API int lbm_get_pops(lbm_h h, int level, double *f_out, int on_device);
  * LBM_ERR_DIVERGED if a NaN or Inf was met. */
 LBM_API int lbm_reduce(lbm_h h, int level, double out[4]);
 
+/* Stream-ordered variant of lbm_reduce, for loops that read a diagnostic after every
+ * step without stalling the GPU.  Enqueues the same reduction (same weights, same
+ * FP64 sums, bitwise equal to lbm_reduce) and a copy of its 4 doubles into out on the
+ * handle's stream, and returns without synchronising.
+ *   - on_device = 0: out is page-locked host memory (cudaHostAlloc, cudaHostRegister,
+ *     a pinned tensor); pageable memory is rejected with LBM_ERR_ARG.  on_device = 1:
+ *     out is device memory of the handle's device.
+ *   - out holds the result once the stream has passed the copy (lbm_synchronize or
+ *     any synchronising call); the caller owns out and keeps it alive until then.
+ *   - NaN or Inf is not reported by the return value: the sums hold it, and the
+ *     device status word records it (lbm_check_status returns LBM_ERR_DIVERGED).
+ *   - Calls on one handle are ordered; each writes only its own out. */
+LBM_API int lbm_reduce_async(lbm_h h, int level, double *out, int on_device);
+
 /* Allocation-free variant of lbm_reduce (the paper has no counterpart; this is a
  * library service).  For callers that may not allocate device memory once they are
  * running -- for instance a host process whose device heap is entirely handed to

@@ -1390,6 +1390,25 @@ int lbm_reduce(lbm_h h, int level, double out[4])
     return LBM_OK;
 }
 
+int lbm_reduce_async(lbm_h h, int level, double *out, int on_device)
+{
+    if (!check_level(h, level)) return LBM_ERR_ARG;
+    if (!out) return fail(h, LBM_ERR_ARG, "out is NULL");
+    cudaPointerAttributes pa{};
+    CK(cudaPointerGetAttributes(&pa, out));
+    if (on_device) {
+        if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)
+            return fail(h, LBM_ERR_ARG, "out is not device memory");
+    } else if (pa.type != cudaMemoryTypeHost) {
+        return fail(h, LBM_ERR_ARG, "out must be page-locked host memory for an asynchronous read");
+    }
+    dispatch(h, [&](auto s) { decltype(s)::reduce(h, level); });
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, h->d_red, 4 * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       h->stream));
+    return LBM_OK;
+}
+
 int lbm_check_status(lbm_h h)
 {
     if (!h) return LBM_ERR_ARG;

@@ -60,6 +60,7 @@ EXPORTS = [
     "lbm_last_error", "lbm_destroy", "lbm_reduce_static", "lbm_create_batch", "lbm_batch_member",
     "lbm_batch_check_barrier", "lbm_set_probes", "lbm_get_probes", "lbm_save_state", "lbm_load_state",
     "lbm_autotune", "lbm_set_tile_config", "lbm_get_tile_config", "lbm_set_interface_mapping",
+    "lbm_reduce_async",
 ]
 TILE_CONFIGS = 5
 IFACE_AUTO, IFACE_NODE, IFACE_SEGMENT = 0, 1, 2
@@ -87,6 +88,7 @@ def lib():
     L.lbm_get_pops.argtypes = [vp, C.c_int, vp, C.c_int]
     L.lbm_reduce.argtypes = [vp, C.c_int, dp]
     L.lbm_reduce_static.argtypes = [vp, C.c_int, dp]
+    L.lbm_reduce_async.argtypes = [vp, C.c_int, vp, C.c_int]
     L.lbm_check_status.argtypes = [vp]
     L.lbm_max_newton_iters.argtypes = [vp]
     L.lbm_timing_enable.argtypes = [vp, C.c_int]
@@ -279,6 +281,22 @@ class Hierarchy:
         out = (C.c_double * 4)()
         self._check(lib().lbm_reduce(self._h, l, out))
         return np.array(out[:])
+
+    def reduce_async(self, l, out):
+        """lbm_reduce_async: enqueue the level's mass and momentum into out (4 float64)
+        without synchronising.  out is page-locked host memory (a pinned CPU tensor or a
+        numpy view of one) or a CUDA tensor; it holds the sums after synchronize()."""
+        if isinstance(out, np.ndarray):
+            if out.dtype != np.float64 or out.size < 4 or not out.flags["C_CONTIGUOUS"]:
+                raise ValueError("out must be a contiguous float64 array of at least 4 values")
+            ptr, dev = out.ctypes.data_as(C.c_void_p), 0
+        else:
+            if out.dtype != self.torch.float64 or out.numel() < 4 or not out.is_contiguous():
+                raise ValueError("out must be a contiguous float64 tensor of at least 4 values")
+            ptr, dev = C.c_void_p(out.data_ptr()), int(out.is_cuda)
+        self._enter(dev)
+        self._check(lib().lbm_reduce_async(self._h, l, ptr, dev))
+        self._leave(dev)
 
     def reduce_static(self, l):
         """lbm_reduce_static: the same sums with the partials in static device memory."""

@@ -1,4 +1,5 @@
-"""Checkpoint/resume and density probes through the C-ABI."""
+"""Checkpoint/resume, density probes and the stream-ordered level reduction through
+the C-ABI."""
 import math
 
 import numpy as np
@@ -92,3 +93,43 @@ def test_probes_sample_interpolated_density():
     want = np.array([_oracle_probe(o, x, y) for x, y in pts[:, :2]])
     assert np.max(np.abs(got[-1] - want)) < 1e-12
     assert np.max(np.abs(got[-1] - 1.0)) > 1e-7  # the pulse has reached the ring
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_async_reduce_equals_reduce_every_step(storage):
+    """lbm_reduce_async enqueued after every coarse step into rows of a pinned host
+    array (and into a CUDA tensor) gives, after one synchronisation, exactly the sums
+    that lbm_reduce returns step by step on a twin hierarchy."""
+    d = W.pulse2d(n=64, boxes=((16, 48), (24, 40)), Rc_finest=3.0, storage=storage)
+    a, b = _make(d), _make(d)
+    K, L = 6, 2
+    rows = torch.zeros((K, 4), dtype=torch.float64).pin_memory()
+    dev = torch.zeros((K, 4), dtype=torch.float64, device="cuda")
+    want = []
+    for k in range(K):
+        a.advance(1)
+        a.reduce_async(L, rows[k])
+        a.reduce_async(0, dev[k])
+        b.advance(1)
+        want.append((b.reduce(L), b.reduce(0)))
+    a.synchronize()
+    torch.cuda.synchronize()
+    for k in range(K):
+        assert np.array_equal(rows[k].numpy(), want[k][0])
+        assert np.array_equal(dev[k].cpu().numpy(), want[k][1])
+    # a numpy view of pinned memory is accepted too
+    view = torch.zeros(4, dtype=torch.float64).pin_memory().numpy()
+    a.reduce_async(1, view)
+    a.synchronize()
+    assert np.array_equal(view, a.reduce(1))
+    a.check_status()
+
+
+def test_async_reduce_rejects_pageable_host_memory():
+    d = W.pulse2d(n=64, boxes=((16, 48), (24, 40)), Rc_finest=3.0, storage="f32")
+    h = _make(d)
+    with pytest.raises(lbm.LbmError) as e:
+        h.reduce_async(0, np.zeros(4))
+    assert e.value.code == lbm.LBM_ERR_ARG
+    with pytest.raises(lbm.LbmError):
+        h.reduce_async(h.n_levels, torch.zeros(4, dtype=torch.float64).pin_memory())
