@@ -1397,8 +1397,10 @@ int lbm_reduce_async(lbm_h h, int level, double *out, int on_device)
     cudaPointerAttributes pa{};
     CK(cudaPointerGetAttributes(&pa, out));
     if (on_device) {
-        if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)
-            return fail(h, LBM_ERR_ARG, "out is not device memory");
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        if ((pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) || pa.device != dev)
+            return fail(h, LBM_ERR_ARG, "out is not device memory of the current device");
     } else if (pa.type != cudaMemoryTypeHost) {
         return fail(h, LBM_ERR_ARG, "out must be page-locked host memory for an asynchronous read");
     }
