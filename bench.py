@@ -579,50 +579,85 @@ def cpu_baseline(workload, steps=None):
 
 
 # pressure scale of the Pa-equivalent error: p' = (rho'/rho0) rho0 c0^2 with
-# rho0 c0^2 = 1.206e5 Pa (air at rest)
+# rho0 c0^2 = 1.206e5 Pa (air at rest); levels in dB re 2e-5 Pa (the usual acoustic
+# reference, which the paper does not state)
 P_REF_PA = 1.206e5
+P_DB_REF_PA = 2e-5
+
+
+def _db(p_pa):
+    import math
+
+    return 20.0 * math.log10(p_pa / P_DB_REF_PA) if p_pa > 0 else float("-inf")
+
+
+def _storage_error(d, st, steps, ref):
+    """Advance description d in storage st on the GPU and compare every level with the
+    oracle's macros ref: (rel Linf rho, rel Linf u, max|drho|, sum drho^2, nodes,
+    max|rho - 1| of the oracle)."""
+    import numpy as np
+
+    from paper_2004_14887_gb300 import lbm
+    from paper_2004_14887_gb300 import workloads as W
+
+    d = _with_storage(d, st)
+    g = lbm.Hierarchy(d)
+    for l in range(g.n_levels):
+        r, u = W.init_fields(d, l)
+        g.init_fields(l, r, u)
+    g.advance(steps)
+    g.check_status()
+    er = eu = ed = 0.0
+    sq, cnt, amp = 0.0, 0, 0.0
+    for l in range(g.n_levels):
+        m = g.node_class(l) != lbm.HOLE
+        rg, ug = g.get_macros(l)
+        ro, uo = ref[l]
+        amp = max(amp, float(np.max(np.abs(ro[m] - 1.0))))
+        dr = rg[m] - ro[m]
+        er = max(er, float(np.max(np.abs(dr)) / np.max(np.abs(ro[m]))))
+        eu = max(eu, float(np.max(np.abs(ug[:, m] - uo[:, m])) / max(np.max(np.abs(uo[:, m])), 1e-300)))
+        ed = max(ed, float(np.max(np.abs(dr))))
+        sq += float(np.sum(dr * dr))
+        cnt += int(m.sum())
+    g.close()
+    return er, eu, ed, sq, cnt, amp
 
 
 def accuracy(workload, storages):
     """The workload's replica advanced on the GPU in each storage and by the FP64
     oracle for the same steps: per storage, the relative L-infinity errors of rho and
     u (worst level), the density error relative to the signal amplitude max|rho - 1|,
-    and the RMS density error as a pressure in Pa-equivalent."""
-    import numpy as np
-
-    from paper_2004_14887_gb300 import lbm
+    and the RMS density error as a pressure in Pa-equivalent and in dB.  The same
+    comparison on a uniform grid (the replica's level 0 with no refinement) gives the
+    storage's precision floor; floor_ratio = RMS error of the refined run / that
+    floor, about 1 when the interface adds no error of its own beyond the storage's."""
+    from oracle import oracle as O
     from paper_2004_14887_gb300 import workloads as W
 
     text, _, steps = REPLICA[workload]
     d64, o, _ = _oracle_run(workload, steps, warm=0)
     ref = [o.macros(l) for l in range(o.n_levels)]
+    du = dict(d64, boxes=[])
+    ou = O.Hierarchy(du)
+    r, u = W.init_fields(du, 0)
+    ou.init(0, r, u)
+    ou.advance(steps)
+    ref_u = [ou.macros(0)]
     out = {}
     for st in storages:
-        d = _with_storage(d64, st)
-        g = lbm.Hierarchy(d)
-        for l in range(g.n_levels):
-            r, u = W.init_fields(d, l)
-            g.init_fields(l, r, u)
-        g.advance(steps)
-        g.check_status()
-        er = eu = ed = 0.0
-        sq, cnt, amp = 0.0, 0, 0.0
-        for l in range(g.n_levels):
-            m = g.node_class(l) != lbm.HOLE
-            rg, ug = g.get_macros(l)
-            ro, uo = ref[l]
-            amp = max(amp, float(np.max(np.abs(ro[m] - 1.0))))
-            dr = rg[m] - ro[m]
-            er = max(er, float(np.max(np.abs(dr)) / np.max(np.abs(ro[m]))))
-            eu = max(eu, float(np.max(np.abs(ug[:, m] - uo[:, m])) / max(np.max(np.abs(uo[:, m])), 1e-300)))
-            ed = max(ed, float(np.max(np.abs(dr))))
-            sq += float(np.sum(dr * dr))
-            cnt += int(m.sum())
-        g.close()
+        er, eu, ed, sq, cnt, amp = _storage_error(d64, st, steps, ref)
+        _, _, _, squ, cntu, _ = _storage_error(du, st, steps, ref_u)
         rms = (sq / max(cnt, 1)) ** 0.5
+        floor = (squ / max(cntu, 1)) ** 0.5
         out[st] = {"rho_rel_linf": er, "u_rel_linf": eu, "drho_rel_amplitude": ed / max(amp, 1e-300),
-                   "dp_rms_pa": rms * P_REF_PA, "dp_max_pa": ed * P_REF_PA, "amplitude_pa": amp * P_REF_PA}
-    return {"vs": "FP64 oracle", "sample": f"{steps} coarse steps of the {text}", "by_storage": out}
+                   "dp_rms_pa": rms * P_REF_PA, "dp_rms_db": _db(rms * P_REF_PA), "dp_max_pa": ed * P_REF_PA,
+                   "amplitude_pa": amp * P_REF_PA, "amplitude_db": _db(amp * P_REF_PA),
+                   "floor_dp_rms_pa": floor * P_REF_PA,
+                   "floor_ratio": rms / floor if floor > 0 else (0.0 if rms == 0 else float("inf"))}
+    return {"vs": "FP64 oracle", "sample": f"{steps} coarse steps of the {text}",
+            "floor": "the same comparison on the replica's level 0 alone (uniform grid, no interface)",
+            "db_ref_pa": P_DB_REF_PA, "by_storage": out}
 
 
 def run_reference(args):
