@@ -527,7 +527,7 @@ def run_gb300(args):
 # the single-threaded oracle within ~10-30 s.
 REPLICA = {
     "pulse2d_3lvl": ("128^2 three-level replica (1/4 of each axis)", 150, 40),
-    "vortex2d_2lvl": ("the workload itself (128^2, two levels)", 150, 40),
+    "vortex2d_2lvl": ("full-size 128^2 two-level hierarchy (no replica needed)", 150, 40),
     "vortex3d_3lvl": ("32^3 three-level replica (1/8 of each axis)", 15, 6),
     "vortex3d_3lvl_128": ("32^3 three-level replica (1/8 of vortex3d_3lvl per axis)", 15, 6),
     "slab3d_3lvl": ("64x64x32 three-level replica (1/8 of each axis)", 3, 2),
