@@ -1110,6 +1110,14 @@ int orc_get_pops(orc_h *h, int l, double *f)
     return 0;
 }
 
+int orc_get_gradients(orc_h *h, int l, double *S, double *C)
+{
+    if (l < 0 || l >= h->nl) return -1;
+    memcpy(S, h->lev[l].S, sizeof(double) * 6 * h->lev[l].N);
+    memcpy(C, h->lev[l].C, sizeof(double) * 6 * h->lev[l].N);
+    return 0;
+}
+
 int orc_set_pops(orc_h *h, int l, const double *f)
 {
     if (l < 0 || l >= h->nl) return -1;

@@ -88,6 +88,12 @@ int orc_advance(orc_h *h, long n_coarse_steps);
 int orc_get_macros(orc_h *h, int l, double *rho, double *u);
 int orc_get_pops(orc_h *h, int l, double *f);
 int orc_set_pops(orc_h *h, int l, const double *f);
+/* S_ab and C_ab = sum_g d_g Psi_abg last supplied to the interface nodes of level l
+ * ([6][N], order xx yy zz xy xz yz; lattice units of level l; zero elsewhere): at a
+ * TF node of a fine level the coarse-stencil values times 1/2, at the co-located
+ * coarse node the unscaled values of the last sync sub-step, at hanging nodes the
+ * interpolated ones. */
+int orc_get_gradients(orc_h *h, int l, double *S, double *C);
 int orc_max_newton_iters(orc_h *h);
 long orc_node_updates(orc_h *h);
 const char *orc_error(orc_h *h);

@@ -70,6 +70,7 @@ def lib():
         L.orc_get_macros.argtypes = [C.c_void_p, C.c_int, dp, dp]
         L.orc_get_pops.argtypes = [C.c_void_p, C.c_int, dp]
         L.orc_set_pops.argtypes = [C.c_void_p, C.c_int, dp]
+        L.orc_get_gradients.argtypes = [C.c_void_p, C.c_int, dp, dp]
         L.orc_max_newton_iters.argtypes = [C.c_void_p]
         L.orc_node_updates.argtypes = [C.c_void_p]
         L.orc_node_updates.restype = C.c_long
@@ -271,6 +272,15 @@ class Hierarchy:
         f = np.zeros((self.q, N))
         lib().orc_get_pops(self._h, l, _dp(f))
         return f
+
+    def gradients(self, l):
+        """(S, C) last supplied to the interface nodes of level l, each [6, N]."""
+        N = self.levels[l]["N"]
+        S = np.zeros((6, N))
+        Cm = np.zeros((6, N))
+        if lib().orc_get_gradients(self._h, l, _dp(S), _dp(Cm)) != 0:
+            raise IndexError(l)
+        return S, Cm
 
     def set_pops(self, l, f):
         f = _f64(f)

@@ -176,3 +176,50 @@ def test_newton_recovers_manufactured_root(q):
     F0, J0 = O.newton_system(q, fhat, gam, Xs + 1e-3)
     X1 = Xs + 1e-3 - np.linalg.solve(J0, F0)
     assert np.max(np.abs(X1 - Xs)) < 50 * 1e-6
+
+
+def test_interface_gradients_match_taylor_green_derivatives():
+    """Sec. 3.3, Eqs. (PijResc) and (PSIResc), readings R8 and R10: the strain rate S
+    and C_ab = sum_g d_g Psi_abg supplied to the interface nodes after one coarse step
+    of a Taylor-Green vortex (u_x = U sin kx cos ky, u_y = -U cos kx sin ky, a steady
+    inviscid flow) equal the analytic derivatives in each level's lattice units: x 1/2
+    at fine TF and hanging nodes, x 1 at the co-located coarse nodes. Measured worst
+    errors: 1.4 % of U k on S_xx and S_yy, 2.8 % on S_xy, 1.0 % of 3 U^3 k on C (the
+    coarse and fine sides' start-up transients differ; the errors halve with each
+    doubling of n). The fine-level S with its factor 1/2 lost (planted in a copy of the
+    oracle) is 72 % off; a wrong sign or swapped axes is as far off."""
+    n, U = 64, 1e-3
+    k = 2 * math.pi / n
+    lo, hi = n // 4, 3 * n // 4
+    h = O.Hierarchy({"lattice": 9, "coarse_n": (n, n), "boxes": [((lo, lo), (hi, hi))], "nu0": 1e-5})
+
+    def coords(l):
+        # the vortex cells are shifted by n/8 so that the outline does not sit on the
+        # zeros of S and C
+        info = h.level_info(l)
+        nx, ny, _ = info["n"]
+        s = 2.0 ** l
+        return (np.tile((np.arange(nx) + info["off"][0]) / s + n / 8, ny),
+                np.repeat((np.arange(ny) + info["off"][1]) / s + n / 8, nx))
+
+    for l in range(2):
+        X, Y = coords(l)
+        u = np.stack([U * np.sin(k * X) * np.cos(k * Y), -U * np.cos(k * X) * np.sin(k * Y)])
+        h.init(l, np.ones(X.size), u)
+    h.advance(1)
+    checked = 0
+    for l, scale, classes in [(1, 0.5, (O.TFP, O.IE)), (0, 1.0, (O.TFC,))]:
+        X, Y = coords(l)
+        S, Cg = h.gradients(l)
+        m = np.isin(h.node_class(l), classes)
+        cx, sx, cy, sy = np.cos(k * X), np.sin(k * X), np.cos(k * Y), np.sin(k * Y)
+        sxx = U * k * cx * cy
+        want = {0: (S[0], sxx), 1: (S[1], -sxx), 3: (S[3], 0.0 * X)}
+        for _, (got, w) in want.items():
+            assert np.max(np.abs(got[m] - scale * w[m])) < 0.04 * scale * U * k
+        c3 = 3 * U ** 3 * k
+        cxx, cyy = c3 * sx ** 2 * cx * cy ** 3, -c3 * cx ** 3 * sy ** 2 * cy
+        assert np.max(np.abs(Cg[0][m] - scale * cxx[m])) < 0.04 * scale * c3
+        assert np.max(np.abs(Cg[1][m] - scale * cyy[m])) < 0.04 * scale * c3
+        checked += int(m.sum())
+    assert checked == 12 * (hi - lo)  # fine outline: 8 (hi - lo) TF and hanging nodes; coarse: 4 (hi - lo)
