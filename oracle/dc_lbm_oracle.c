@@ -413,6 +413,16 @@ void orc_known_from_occupancy(int lattice, const unsigned char *occ_f, const uns
 /* ------------------------------------------------------------------------ */
 /* Hierarchy (Sec. 3.5 steps, recursive 2:1 sub-cycling)                     */
 /* ------------------------------------------------------------------------ */
+/* Every per-node loop of a step writes only its own node (and, in the coarse
+ * rebuild, the one coarse node co-located with it), so the loops may run their
+ * nodes in any order.  Built with -fopenmp they are shared out over threads; the
+ * arithmetic of each node is unchanged, so both builds give identical bits.
+ * Without -fopenmp the pragma is ignored and the loops run in index order. */
+#ifdef _OPENMP
+#define ORC_NODE_LOOP _Pragma("omp parallel for schedule(static)")
+#else
+#define ORC_NODE_LOOP
+#endif
 typedef struct {
     long n[3], off[3], N;
     int periodic[3];
@@ -730,6 +740,7 @@ static void stream_level(orc_h *h, int l)
 {
     level_t *v = &h->lev[l];
     int Q = h->L.Q;
+    ORC_NODE_LOOP
     for (long idx = 0; idx < v->N; idx++) {
         if (v->cls[idx] == ORC_HOLE) continue;
         long p[3];
@@ -749,6 +760,7 @@ static void push_history(orc_h *h, int l)
     int Q = h->L.Q;
     int slot = (int)((v->nsteps + 1) % 3);
     memcpy(v->hg[slot], v->g, sizeof(double) * Q * v->N);
+    ORC_NODE_LOOP
     for (long idx = 0; idx < v->N; idx++) {
         if (v->cls[idx] != ORC_BULK) continue;
         double r, uu[3];
@@ -791,6 +803,8 @@ static void reconstruct_tf(orc_h *h, int l, int phase)
     int slot[3];
     double wt[3];
     parent_time_weights(h, l, phase, slot, wt);
+    int worst = 0; /* largest Newton count, -1 once a node did not converge */
+    ORC_NODE_LOOP
     for (long idx = 0; idx < v->N; idx++) {
         if (v->cls[idx] != ORC_TFP) continue;
         long p[3], pc[3];
@@ -816,10 +830,18 @@ static void reconstruct_tf(orc_h *h, int l, int phase)
         }
         int it = newton_lat(&h->L, fhat, Gam, X);
         if (it < 0) {
-            set_err(h, "Newton did not converge in 10 iterations");
-            return;
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            worst = -1;
+            continue;
         }
-        if (it > h->max_newton) h->max_newton = it;
+#ifdef _OPENMP
+#pragma omp critical(orc_newton_count)
+#endif
+        {
+            if (worst >= 0 && it > worst) worst = it;
+        }
         feq_lat(&h->L, X[0], X + 1, feq);
         for (int i = 0; i < Q; i++)
             if (gam_c[i]) v->g[(size_t)i * v->N + idx] = feq[i] + R * (fhat[i] - feq[i]);
@@ -832,11 +854,17 @@ static void reconstruct_tf(orc_h *h, int l, int phase)
             for (int a = 0; a < 3; a++) pv->u[(size_t)a * pv->N + cidx] = a < D ? X[1 + a] : 0.0;
         }
     }
+    if (worst < 0) {
+        set_err(h, "Newton did not converge in 10 iterations");
+        return;
+    }
+    if (worst > h->max_newton) h->max_newton = worst;
 }
 
 static void bulk_macros(orc_h *h, int l)
 {
     level_t *v = &h->lev[l];
+    ORC_NODE_LOOP
     for (long idx = 0; idx < v->N; idx++) {
         if (v->cls[idx] != ORC_BULK) continue;
         double r, uu[3];
@@ -887,11 +915,14 @@ static void tf_gradients(orc_h *h, int l, int phase)
     int slot[3];
     double wt[3];
     parent_time_weights(h, l, phase, slot, wt);
+    int bad = 0;
+    ORC_NODE_LOOP
     for (long idx = 0; idx < v->N; idx++) {
         if (v->cls[idx] != ORC_TFP) continue;
         long p[3];
         coords_of(v, idx, p);
         double mr[3][2], mu[3][2][3];
+        int ok = 1;
         for (int b = 0; b < D; b++)
             for (int s = 0; s < 2; s++) {
                 long y[3] = {p[0], p[1], p[2]};
@@ -904,8 +935,8 @@ static void tf_gradients(orc_h *h, int l, int phase)
                     long yc[3] = {y[0] / 2, y[1] / 2, y[2] / 2};
                     long jc = node_at(h, l - 1, yc);
                     if (jc < 0 || pv->cls[jc] != ORC_BULK) {
-                        set_err(h, "TF gradient stencil leaves the parent's bulk");
-                        return;
+                        ok = 0;
+                        continue;
                     }
                     double r = 0.0, uu[3] = {0, 0, 0};
                     for (int k = 0; k < 3; k++) {
@@ -917,6 +948,13 @@ static void tf_gradients(orc_h *h, int l, int phase)
                     for (int a = 0; a < 3; a++) mu[b][s][a] = uu[a];
                 }
             }
+        if (!ok) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            bad = 1;
+            continue;
+        }
         double Sc[6], Cc[6];
         gradients_from(h, mr, mu, 1.0, Sc, Cc); /* coarse units: neighbours one coarse cell away */
         for (int k = 0; k < 6; k++) {
@@ -932,6 +970,7 @@ static void tf_gradients(orc_h *h, int l, int phase)
             }
         }
     }
+    if (bad) set_err(h, "TF gradient stencil leaves the parent's bulk");
 }
 
 /* steps 2g / 3e: 4-point 1-D Lagrange along the interface (tensor order over
@@ -944,8 +983,11 @@ static void ie_complete(orc_h *h, int l)
     double wc[4], wo[4];
     orc_lagrange4_weights(0, wc);
     orc_lagrange4_weights(1, wo);
+    int bad = 0;
+    ORC_NODE_LOOP
     for (long idx = 0; idx < v->N; idx++) {
         if (v->cls[idx] != ORC_IE) continue;
+        int ok = 1;
         long p[3], q[3];
         coords_of(v, idx, p);
         for (int a = 0; a < 3; a++) q[a] = p[a] - v->off[a];
@@ -992,8 +1034,8 @@ static void ie_complete(orc_h *h, int l)
                     double wgt = wts[0][i0] * wts[1][i1] * wts[2][i2];
                     long j = node_at(h, l, y);
                     if (j < 0 || v->cls[j] != ORC_TFP) {
-                        set_err(h, "hanging-node stencil does not land on TF nodes");
-                        return;
+                        ok = 0;
+                        continue;
                     }
                     for (int i = 0; i < Q; i++) acc_f[i] += wgt * v->g[(size_t)i * v->N + j];
                     for (int k = 0; k < 6; k++) {
@@ -1001,6 +1043,13 @@ static void ie_complete(orc_h *h, int l)
                         acc_C[k] += wgt * v->C[(size_t)k * v->N + j];
                     }
                 }
+        if (!ok) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            bad = 1;
+            continue;
+        }
         for (int i = 0; i < Q; i++)
             if (!((v->kf[idx] >> i) & 1u)) v->g[(size_t)i * v->N + idx] = acc_f[i];
         for (int k = 0; k < 6; k++) {
@@ -1012,6 +1061,7 @@ static void ie_complete(orc_h *h, int l)
         v->rho[idx] = r;
         for (int a = 0; a < 3; a++) v->u[(size_t)a * v->N + idx] = uu[a];
     }
+    if (bad) set_err(h, "hanging-node stencil does not land on TF nodes");
 }
 
 /* steps 2h / 3g: collision of every node; bulk nodes use the centred
@@ -1020,6 +1070,9 @@ static void collide_level(orc_h *h, int l)
 {
     level_t *v = &h->lev[l];
     int Q = h->L.Q, D = h->L.D;
+    long active = 0;
+    for (long idx = 0; idx < v->N; idx++) active += v->cls[idx] != ORC_HOLE;
+    ORC_NODE_LOOP
     for (long idx = 0; idx < v->N; idx++) {
         unsigned char c = v->cls[idx];
         if (c == ORC_HOLE) continue;
@@ -1048,8 +1101,8 @@ static void collide_level(orc_h *h, int l)
         for (int a = 0; a < 3; a++) uu[a] = v->u[(size_t)a * v->N + idx];
         collide_lat(&h->L, fin, v->rho[idx], uu, S6, C6, v->tau, h->d.sigma, h->d.psi_sign, fout);
         for (int i = 0; i < Q; i++) v->f[(size_t)i * v->N + idx] = fout[i];
-        h->updates++;
     }
+    h->updates += active;
 }
 
 /* Sec. 3.5: one step of level l (async phase 0 / sync phase 1 for l > 0),
@@ -1126,4 +1179,20 @@ int orc_set_pops(orc_h *h, int l, const double *f)
 }
 
 int orc_max_newton_iters(orc_h *h) { return h->max_newton; }
+
+/* Threads of the node loops: sets the count when n > 0 and returns the count in use
+ * (1 in the build without OpenMP). */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int orc_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 long orc_node_updates(orc_h *h) { return h->updates; }

@@ -97,6 +97,9 @@ int orc_get_gradients(orc_h *h, int l, double *S, double *C);
 int orc_max_newton_iters(orc_h *h);
 long orc_node_updates(orc_h *h);
 const char *orc_error(orc_h *h);
+/* threads of the per-node loops (OpenMP build): sets the count when n > 0, returns
+ * the count in use; 1 in the plain build.  Both builds compute identical bits. */
+int orc_threads(int n);
 
 #ifdef __cplusplus
 }

@@ -17,21 +17,31 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblbm_oracle.so")
+# the same source built with -fopenmp: the per-node loops of a step are shared out
+# over threads, every node's arithmetic is unchanged (identical bits)
+LIB_OMP_PATH = os.path.join(HERE, "liblbm_oracle_omp.so")
 SRC = os.path.join(HERE, "dc_lbm_oracle.c")
 
 HOLE, BULK, TFP, IE, TFC = 0, 1, 2, 3, 4
 MAX_LEVELS = 4
 
 
+def _gcc(out, extra):
+    src_t = max(os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "dc_lbm_oracle.h")))
+    if not os.path.exists(out) or os.path.getmtime(out) < src_t:
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", *extra,
+                               "-o", out, SRC, "-lm"])
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (single translation unit, -O2, no -ffast-math)."""
-    if force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < max(
-        os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "dc_lbm_oracle.h"))
-    ):
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
-             "-o", LIB_PATH, SRC, "-lm"]
-        )
+    """Compile the oracle with gcc (single translation unit, -O2, no -ffast-math, no
+    contraction), once plain and once with -fopenmp."""
+    if force:
+        for p in (LIB_PATH, LIB_OMP_PATH):
+            if os.path.exists(p):
+                os.remove(p)
+    _gcc(LIB_PATH, [])
+    _gcc(LIB_OMP_PATH, ["-fopenmp"])
     return LIB_PATH
 
 
@@ -49,14 +59,14 @@ class _Desc(C.Structure):
     ]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
+def lib(threaded: bool = False):
+    """The plain build, or with threaded=True the OpenMP build."""
+    if threaded not in _libs:
         build()
-        L = C.CDLL(LIB_PATH)
+        L = C.CDLL(LIB_OMP_PATH if threaded else LIB_PATH)
         dp = C.POINTER(C.c_double)
         L.orc_create.restype = C.c_void_p
         L.orc_create.argtypes = [C.POINTER(_Desc), C.c_char_p, C.c_int]
@@ -88,8 +98,14 @@ def lib():
         L.orc_tempint_weights.argtypes = [dp]
         L.orc_lagrange4_weights.argtypes = [C.c_int, dp]
         L.orc_known_from_occupancy.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
-        _lib = L
-    return _lib
+        L.orc_threads.argtypes = [C.c_int]
+        _libs[threaded] = L
+    return _libs[threaded]
+
+
+def threads(n: int = 0) -> int:
+    """Threads of the OpenMP build's node loops: sets the count when n > 0; returns it."""
+    return lib(True).orc_threads(int(n))
 
 
 def _dp(a: np.ndarray):
@@ -191,9 +207,12 @@ class Hierarchy:
 
     desc keys: lattice (9|19), coarse_n (nx, ny[, nz]), boxes [((lo),(hi)), ...]
     for levels 1.. in level-0 cell units, nu0, sigma, dc_variant, psi_sign.
+    threaded=True runs the per-node loops of every step on the OpenMP build (same
+    arithmetic per node, identical results).
     """
 
-    def __init__(self, desc: dict):
+    def __init__(self, desc: dict, threaded: bool = False):
+        self._L = lib(threaded)
         d = _Desc()
         d.lattice = int(desc["lattice"])
         boxes = desc.get("boxes", [])
@@ -210,7 +229,7 @@ class Hierarchy:
         d.dc_variant = int(desc.get("dc_variant", 2))
         d.psi_sign = int(desc.get("psi_sign", -1))
         err = C.create_string_buffer(256)
-        self._h = lib().orc_create(C.byref(d), err, 256)
+        self._h = self._L.orc_create(C.byref(d), err, 256)
         if not self._h:
             raise ValueError("oracle: " + err.value.decode())
         self.q = d.lattice
@@ -221,7 +240,7 @@ class Hierarchy:
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
-            lib().orc_destroy(h)
+            self._L.orc_destroy(h)
             self._h = None
 
     def level_info(self, l):
@@ -229,7 +248,7 @@ class Hierarchy:
         off = (C.c_long * 3)()
         per = (C.c_int * 3)()
         tau = C.c_double()
-        if lib().orc_level_info(self._h, l, n, off, per, C.byref(tau)) != 0:
+        if self._L.orc_level_info(self._h, l, n, off, per, C.byref(tau)) != 0:
             raise IndexError(l)
         return {"n": tuple(n), "off": tuple(off), "periodic": tuple(per), "tau": tau.value,
                 "N": n[0] * n[1] * n[2]}
@@ -237,14 +256,14 @@ class Hierarchy:
     def node_class(self, l):
         N = self.levels[l]["N"]
         out = np.zeros(N, dtype=np.uint8)
-        lib().orc_node_class(self._h, l, out.ctypes.data_as(C.c_void_p))
+        self._L.orc_node_class(self._h, l, out.ctypes.data_as(C.c_void_p))
         return out
 
     def known_masks(self, l):
         N = self.levels[l]["N"]
         kf = np.zeros(N, dtype=np.uint32)
         kc = np.zeros(N, dtype=np.uint32)
-        lib().orc_known_masks(self._h, l, kf.ctypes.data_as(C.c_void_p), kc.ctypes.data_as(C.c_void_p))
+        self._L.orc_known_masks(self._h, l, kf.ctypes.data_as(C.c_void_p), kc.ctypes.data_as(C.c_void_p))
         return kf, kc
 
     def init(self, l, rho, u):
@@ -253,24 +272,24 @@ class Hierarchy:
         u3 = np.zeros((3, N))
         u = np.asarray(u, dtype=np.float64).reshape(-1, N)
         u3[: u.shape[0]] = u
-        if lib().orc_init(self._h, l, _dp(rho), _dp(np.ascontiguousarray(u3))) != 0:
+        if self._L.orc_init(self._h, l, _dp(rho), _dp(np.ascontiguousarray(u3))) != 0:
             raise RuntimeError("orc_init failed")
 
     def advance(self, n):
-        if lib().orc_advance(self._h, int(n)) != 0:
-            raise RuntimeError("oracle: " + lib().orc_error(self._h).decode())
+        if self._L.orc_advance(self._h, int(n)) != 0:
+            raise RuntimeError("oracle: " + self._L.orc_error(self._h).decode())
 
     def macros(self, l):
         N = self.levels[l]["N"]
         rho = np.zeros(N)
         u = np.zeros((self.D, N))
-        lib().orc_get_macros(self._h, l, _dp(rho), _dp(u))
+        self._L.orc_get_macros(self._h, l, _dp(rho), _dp(u))
         return rho, u
 
     def pops(self, l):
         N = self.levels[l]["N"]
         f = np.zeros((self.q, N))
-        lib().orc_get_pops(self._h, l, _dp(f))
+        self._L.orc_get_pops(self._h, l, _dp(f))
         return f
 
     def gradients(self, l):
@@ -278,18 +297,18 @@ class Hierarchy:
         N = self.levels[l]["N"]
         S = np.zeros((6, N))
         Cm = np.zeros((6, N))
-        if lib().orc_get_gradients(self._h, l, _dp(S), _dp(Cm)) != 0:
+        if self._L.orc_get_gradients(self._h, l, _dp(S), _dp(Cm)) != 0:
             raise IndexError(l)
         return S, Cm
 
     def set_pops(self, l, f):
         f = _f64(f)
-        lib().orc_set_pops(self._h, l, _dp(f))
+        self._L.orc_set_pops(self._h, l, _dp(f))
 
     @property
     def max_newton_iters(self):
-        return lib().orc_max_newton_iters(self._h)
+        return self._L.orc_max_newton_iters(self._h)
 
     @property
     def node_updates(self):
-        return lib().orc_node_updates(self._h)
+        return self._L.orc_node_updates(self._h)
