@@ -58,12 +58,20 @@ def n_levels(desc: dict) -> int:
     return 1 + len(desc.get("boxes", []))
 
 
-def level_positions(desc: dict, l: int):
-    """Node positions of level l in level-0 units, arrays of shape (nz, ny, nx)."""
+def level_axes(desc: dict, l: int):
+    """Node positions of level l in level-0 units along each axis, shaped to broadcast
+    to (nz, ny, nx): x (1, 1, nx), y (1, ny, 1), z (nz, 1, 1)."""
     n, off, _ = level_geometry(desc, l)
     s = 1.0 / (1 << l)
-    z, y, x = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
-    return ((x + off[0]) * s, (y + off[1]) * s, (z + off[2]) * s)
+    return ((np.arange(n[0]) + off[0]) * s).reshape(1, 1, -1), ((np.arange(n[1]) + off[1]) * s).reshape(1, -1, 1), \
+        ((np.arange(n[2]) + off[2]) * s).reshape(-1, 1, 1)
+
+
+def level_positions(desc: dict, l: int):
+    """Node positions of level l in level-0 units, arrays of shape (nz, ny, nx)."""
+    n, _, _ = level_geometry(desc, l)
+    shape = (n[2], n[1], n[0])
+    return tuple(np.broadcast_to(a, shape).copy() for a in level_axes(desc, l))
 
 
 def level_int_coords(desc: dict, l: int):
@@ -243,7 +251,12 @@ def slab3d(nxy=512, nz=256, slab=(96, 160), box=((128, 128, 112), (384, 384, 144
 def init_fields(desc: dict, l: int):
     """(rho, u) of every node of level l, rho shape (N,), u shape (D, N)."""
     D = 2 if desc["lattice"] == 9 else 3
-    x, y, z = level_positions(desc, l)
+    # per-axis positions: every field below is evaluated by broadcasting (the same
+    # per-node arithmetic as on full coordinate arrays) and expanded to the level's
+    # box at the end
+    x, y, z = level_axes(desc, l)
+    n, _, _ = level_geometry(desc, l)
+    shape = (n[2], n[1], n[0])
     ini = desc["init"]
     cn = list(desc["coarse_n"]) + [1] * (3 - len(desc["coarse_n"]))
     per = (float(cn[0]), float(cn[1]), float(cn[2]))
@@ -259,11 +272,12 @@ def init_fields(desc: dict, l: int):
                                           ini["U"], per)
         rho = rho_v * rho_p
     elif ini["kind"] == "uniform":
-        rho = np.full_like(x, ini.get("rho", 1.0))
+        rho = np.full(shape, ini.get("rho", 1.0))
         U = ini["U"]
-        ux, uy, uz = np.full_like(x, U[0]), np.full_like(x, U[1]), np.full_like(x, U[2] if len(U) > 2 else 0.0)
+        ux, uy, uz = np.full(shape, U[0]), np.full(shape, U[1]), np.full(shape, U[2] if len(U) > 2 else 0.0)
     else:
         raise ValueError(ini["kind"])
+    rho, ux, uy, uz = (np.broadcast_to(np.asarray(a, dtype=np.float64), shape) for a in (rho, ux, uy, uz))
     if ini.get("noise", 0.0) > 0.0:
         ix, iy, iz = level_int_coords(desc, l)
         amp = ini["noise"] * math.sqrt(sum(v * v for v in ini["U"]))
@@ -271,8 +285,10 @@ def init_fields(desc: dict, l: int):
         uy = uy + amp * hashed_normal(ini.get("seed", 0), 2, ix, iy, iz)
         if D == 3:
             uz = uz + amp * hashed_normal(ini.get("seed", 0), 3, ix, iy, iz)
-    u = np.stack([ux, uy, uz][:D]).reshape(D, -1)
-    return np.ascontiguousarray(rho.reshape(-1)), np.ascontiguousarray(u)
+    u = np.empty((D,) + shape)
+    for a, v in enumerate([ux, uy, uz][:D]):
+        u[a] = v
+    return np.ascontiguousarray(rho).reshape(-1), u.reshape(D, -1)
 
 
 def batch2d(n=96, steps=1000, seed=0, storage="f32", nu0=1e-5, sides=(96, 128, 192, 256, 384, 512, 768, 1024)):
