@@ -1,15 +1,19 @@
 #!/usr/bin/env python
 """Throughput of the multi-level DC2 / H-RR lattice Boltzmann hot path on GB300.
 
-Workload: the D2Q9 three-level nested-patch acoustic pulse (coarse 512^2
-periodic, patches of 256^2 and 128^2 coarse cells, Mach-0.2 mean flow, pulse
-amplitude 1e-3), FP32 population storage for the headline value, FP64 and FP16
-(shifted) storage reported beside it.  One step = one coarse step = 1 step of
-level 0, 2 of level 1 and 4 of level 2 (1.65 M node updates, 16.8 M
-fine-equivalent updates).  Inputs live in HBM when timing starts; the L2 is
-flushed (256 MB write) before every timed step, outside the timed events.
+Headline workload (the largest single-GPU configuration): the D3Q19 three-level
+slab hierarchy, coarse 512x512x256, a level-1 slab spanning x and y (z in
+[96,160)) and a level-2 box [128,384)^2 x [112,144), 0.305 G active nodes, an
+acoustic pulse (1e-4) and a vortex in a Mach-0.15 mean flow, FP16 storage of
+f_i - w_i with FP32 arithmetic.  One step = one coarse step = 1 step of level 0,
+2 of level 1 and 4 of level 2 (0.83 G node updates, 17.2 G fine-equivalent).
+FP64, FP32 and FP16 of f_i - f_i^eq(1, U) are reported beside it ("variants"),
+and the other configurations each with their own roofline ("extras").  Inputs
+live in HBM when timing starts; the L2 is flushed (256 MB write) before every
+timed step, outside the timed events.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                    [--workload W] [--storage S]
 
 For N > 1 (torchrun) every rank advances an independent replica of the same
 hierarchy (the single hierarchy does not shard; replicas only); the value is
@@ -147,11 +151,14 @@ WORKLOAD_TEXT = {
                    "[128,384)^2 x [112,144), pulse 1e-4 + vortex at Mach 0.15",
     "vortex3d_3lvl_128": "vortex3d_3lvl_128: D3Q19, 3 levels, coarse 128^3 periodic, cubes 64^3 and 32^3 coarse "
                          "cells (half-size replica of vortex3d_3lvl, for profiling)",
+    "slab3d_3lvl_256": "slab3d_3lvl_256: D3Q19, 3 levels, coarse 256x256x128, slab z in [48,80) and box "
+                       "[64,192)^2 x [56,72) (half-size replica of slab3d_3lvl per axis, for profiling)",
     "batch2d": "batch2d: 96 independent D2Q9 2-level hierarchies, coarse sides drawn from {96..1024}, centred "
                "patches of half the side, seeded vortices or pulses, one persistent cooperative launch per step",
 }
 DEFAULT_STORAGE = {"pulse2d_3lvl": "f32", "vortex2d_2lvl": "f64", "vortex3d_3lvl": "f32", "slab3d_3lvl": "f16s",
-                   "vortex3d_3lvl_128": "f32", "batch2d": "f32"}
+                   "slab3d_3lvl_256": "f16s", "vortex3d_3lvl_128": "f32", "batch2d": "f32"}
+DEFAULT_WORKLOAD = "slab3d_3lvl"
 
 
 def _workloads():
@@ -159,6 +166,8 @@ def _workloads():
 
     return {"pulse2d_3lvl": W.pulse2d, "vortex2d_2lvl": W.vortex2d, "vortex3d_3lvl": W.vortex3d,
             "slab3d_3lvl": W.slab3d,
+            "slab3d_3lvl_256": lambda **kw: W.slab3d(nxy=256, nz=128, slab=(48, 80), box=((64, 64, 56), (192, 192, 72)),
+                                                     **kw),
             "vortex3d_3lvl_128": lambda **kw: W.vortex3d(n=128, boxes=((32, 96), (48, 80)), **kw),
             "batch2d": W.batch2d}
 
@@ -199,7 +208,123 @@ def _traffic_from_profiles(workload, storage):
     return None
 
 
-def run_batch(args):
+_FIELDS = {}
+
+
+def _fields(d, l):
+    """Initial (rho, u) of level l of a workload, computed once per (workload, level)
+    and shared by every hierarchy of the run built from it (storage forms differ only
+    in how the library stores the same state)."""
+    from paper_2004_14887_gb300 import workloads as W
+
+    key = (d.get("name"), json.dumps(d["boxes"]), json.dumps(d["init"], sort_keys=True), l)
+    if key not in _FIELDS:
+        _FIELDS[key] = W.init_fields(d, l)
+    return _FIELDS[key]
+
+
+def _flush_buffer():
+    import torch
+
+    return torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def measure_hierarchy(workload, storage, K, Wm, flush, *, sampler_dev=None, autotune=True, ws=1, timing_steps=None,
+                      label=None):
+    """Device-timed coarse steps of one hierarchy (CUDA events on the library's stream
+    around every step, the L2 flushed before each, outside the events) and the
+    average duration of the dominant kernel, the finest level's bulk collide-and-stream
+    launch (the library's per-launch CUDA events, lbm_timing_*)."""
+    import torch
+
+    from paper_2004_14887_gb300 import lbm
+    from paper_2004_14887_gb300 import workloads as W
+
+    d = _with_storage(_workloads()[workload](), storage)
+    tc = time.perf_counter()
+    h = lbm.Hierarchy(d)
+    setup_s = time.perf_counter() - tc
+    tuned = None
+    if autotune:
+        tuned = h.autotune(reps=10)["cfg"]
+    for l in range(h.n_levels):
+        r, u = _fields(d, l)
+        h.init_fields(l, r, u)
+    print(f"[bench] {label or workload} {storage}: set-up {setup_s:.2f} s, {h.device_bytes() / 1e9:.2f} GB on the "
+          f"device, tile configurations {tuned}", file=sys.stderr, flush=True)
+    h.advance(Wm)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    n0 = h.launch_count()
+    _barrier(ws)
+    torch.cuda.synchronize()
+    clocks = None
+
+    def loop():
+        for k in range(K):
+            flush.zero_()
+            starts[k].record()
+            h.advance(1)
+            ends[k].record()
+        torch.cuda.synchronize()
+
+    if sampler_dev is not None:
+        with ClockSampler(sampler_dev) as cs:
+            loop()
+        clocks = cs.summary()
+    else:
+        loop()
+    _barrier(ws)
+    h.check_status()
+    dev_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
+    launches = h.launch_count() - n0
+    t = max_over_ranks(dev_ms, device="cuda") / 1e3
+    upd = W.updates_per_coarse_step(d)
+    feq = W.fine_equivalent_per_coarse_step(d)
+    L = h.n_levels
+    # dominant kernel: the bulk collide-and-stream launch of the finest level
+    h.timing_enable(True)
+    for _ in range(timing_steps or min(K, 200)):
+        flush.zero_()
+        h.advance(1)
+    ms, cnt = h.timing_read()
+    h.timing_enable(False)
+    bulk_ms = [m / max(c, 1) for m, c in zip(ms, cnt)]
+    nact = [h.levels[l]["n_active"] for l in range(L)]
+    bpp = BYTES_PER_POP[storage]
+    bytes_finest = nact[L - 1] * 2 * h.q * bpp
+    peak, peak_src = _peaks()
+    achieved = bytes_finest / (bulk_ms[L - 1] * 1e-3) / 1e9
+    kname = "k_bulk3d" if h.q == 19 else "k_bulk2d"
+    out = {
+        "value": ws * feq * K / t / 1e6, "actual_mlups": ws * upd * K / t / 1e6, "ms_per_step": 1e3 * t / K,
+        "steps": K, "warmup": Wm, "storage": storage, "gpu_launches": launches, "clocks": clocks,
+        "node_updates_per_step": upd, "fine_equivalent_updates_per_step": feq, "active_nodes_per_level": nact,
+        "bulk_ms_per_launch_by_level": bulk_ms, "tile_config_per_level": tuned,
+        "device_bytes": h.device_bytes(), "setup_s": setup_s,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": _traffic_from_profiles(workload, storage),
+                     "kernel": f"{kname}, bulk collide-and-stream of the finest level (level {L - 1}, "
+                               f"{nact[L - 1]} active nodes, {2 ** (L - 1)} launches per step)",
+                     "algorithmic_bytes_per_launch": bytes_finest, "avg_launch_ms": bulk_ms[L - 1],
+                     "peak_source": f"{peak_src} hbm_gbs (of {peak_src})"},
+        "step_roofline_frac": upd * 2 * h.q * bpp / (t / K) / 1e9 / peak,
+    }
+    h.close()
+    del h
+    torch.cuda.synchronize()
+    return out
+
+
+def measure_batch(storage, K, Wm, flush, *, sampler_dev=None, ws=1):
     """The batched workload: every step advances all hierarchies of the batch by one
     coarse step in one cooperative persistent launch."""
     import torch
@@ -207,89 +332,159 @@ def run_batch(args):
     from paper_2004_14887_gb300 import lbm
     from paper_2004_14887_gb300 import workloads as W
 
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
-    torch.cuda.set_stream(torch.cuda.Stream())
-    if ws > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    storage = args.storage or DEFAULT_STORAGE["batch2d"]
     descs = [_with_storage(d, storage) for d in W.batch2d()]
     tc = time.perf_counter()
     b = lbm.Batch(descs)
     for d, m in zip(descs, b.members):
         for l in range(m.n_levels):
-            r, u = W.init_fields(d, l)
+            r, u = _fields(d, l)
             m.init_fields(l, r, u)
     print(f"[bench] batch2d {storage}: {len(descs)} hierarchies, set-up {time.perf_counter() - tc:.2f} s, "
           f"{b.device_bytes() / 1e9:.2f} GB on the device", file=sys.stderr, flush=True)
     upd = sum(W.updates_per_coarse_step(d) for d in descs)
     feq = sum(W.fine_equivalent_per_coarse_step(d) for d in descs)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    K, Wm = args.steps, args.warmup
     b.advance(Wm)
     torch.cuda.synchronize()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     n0 = b.launch_count()
-    if ws > 1:
-        torch.distributed.barrier()
+    _barrier(ws)
     torch.cuda.synchronize()
-    with ClockSampler(local) as cs:
+    clocks = None
+
+    def loop():
         for k in range(K):
             flush.zero_()
             starts[k].record()
             b.advance(1)
             ends[k].record()
         torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
+
+    if sampler_dev is not None:
+        with ClockSampler(sampler_dev) as cs:
+            loop()
+        clocks = cs.summary()
+    else:
+        loop()
+    _barrier(ws)
     b.check_status()
     ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
-    if ws > 1:
-        t_ = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t_, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t_.item())
-    t = ms / 1e3
+    t = max_over_ranks(ms, device="cuda") / 1e3
     peak, peak_src = _peaks()
     bytes_step = upd * 2 * 9 * BYTES_PER_POP[storage]
-    line = {
-        "metric": METRIC, "value": ws * feq * K / t / 1e6, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
-        "ms_per_step": 1e3 * t / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": storage, "data": "synthetic (seeded analytic fields, no dataset)",
-        "config": {"workload": WORKLOAD_TEXT["batch2d"] + f", {storage} storage", "hierarchies": len(descs),
-                   "node_updates_per_step": upd, "fine_equivalent_updates_per_step": feq,
-                   "l2": "flushed (256 MB write) before every timed step",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
-        "actual_mlups": ws * upd * K / t / 1e6,
+    out = {
+        "value": ws * feq * K / t / 1e6, "actual_mlups": ws * upd * K / t / 1e6, "ms_per_step": 1e3 * t / K,
+        "steps": K, "warmup": Wm, "storage": storage, "hierarchies": len(descs), "gpu_launches": b.launch_count() - n0,
+        "clocks": clocks, "node_updates_per_step": upd, "fine_equivalent_updates_per_step": feq,
         "roofline": {"bound": "hbm", "achieved": bytes_step / (t / K) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": bytes_step / (t / K) / 1e9 / peak, "traffic": None,
                      "kernel": "k_batch (the whole step is one persistent launch)",
                      "algorithmic_bytes_per_launch": bytes_step, "avg_launch_ms": 1e3 * t / K,
-                     "peak_source": f"{peak_src} hbm_gbs"},
-        "gpu_launches": b.launch_count() - n0,
-        "clocks": cs.summary(),
-        "e2e": None,
+                     "peak_source": f"{peak_src} hbm_gbs (of {peak_src})"},
     }
     b.close()
-    if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        line["cpu_baseline"] = cpu_baseline("batch2d", args.cpu_steps)
-        line["accuracy"] = accuracy("batch2d", [storage])
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if ws > 1:
-        torch.distributed.destroy_process_group()
+    torch.cuda.synchronize()
+    return out
 
 
-def run_gb300(args):
-    import numpy as np
+def measure_e2e(workload, storage, K, ws=1):
+    """End to end through the public API with host buffers: the initial fields from
+    pinned host memory (H2D), then every step advances and copies the finest level's
+    FP64 mass and momentum into its row of a pinned host array (D2H, lbm_reduce_async,
+    stream-ordered), and at the end the macros of every level (D2H, synchronising);
+    the handle is set up as a user would: created, initialised, autotuned."""
     import torch
 
     from paper_2004_14887_gb300 import lbm
     from paper_2004_14887_gb300 import workloads as W
 
-    WORKLOADS = _workloads()
+    de = _with_storage(_workloads()[workload](), storage)
+    he = lbm.Hierarchy(de)
+    fields = []
+    for l in range(he.n_levels):
+        r, u = _fields(de, l)
+        rp = torch.from_numpy(r).pin_memory().numpy()
+        up = torch.from_numpy(u).pin_memory().numpy()
+        fields.append((rp, up))
+        he.init_fields(l, rp, up)
+    he.autotune(reps=10)
+    outs = [(torch.empty(he.levels[l]["N"], dtype=torch.float64).pin_memory().numpy(),
+             torch.empty((he.D, he.levels[l]["N"]), dtype=torch.float64).pin_memory().numpy())
+            for l in range(he.n_levels)]
+    sums = torch.zeros((K, 4), dtype=torch.float64).pin_memory()
+    # warm-up on the workload's own state (graph capture); the timed region starts
+    # again from the initial fields
+    he.advance(3)
+    he.check_status()
+    torch.cuda.synchronize()
+    _barrier(ws)
+    te = time.perf_counter()
+    for l in range(he.n_levels):
+        he.init_fields(l, *fields[l])
+    for k in range(K):
+        he.advance(1)
+        he.reduce_async(he.n_levels - 1, sums[k])
+    for l in range(he.n_levels):
+        he.get_macros(l, out=outs[l])
+    torch.cuda.synchronize()
+    _barrier(ws)
+    tw = max_over_ranks(time.perf_counter() - te, device="cuda")
+    he.check_status()
+    if not bool(torch.isfinite(sums).all()):
+        raise RuntimeError("end-to-end run: non-finite mass or momentum")
+    h2d = sum(a.nbytes + b.nbytes for a, b in fields)
+    d2h = sum(a.nbytes + b.nbytes for a, b in outs) + sums.numel() * 8
+    feq = W.fine_equivalent_per_coarse_step(de)
+    he.close()
+    del he, outs, fields
+    torch.cuda.synchronize()
+    return {"value": ws * feq * K / tw / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
+            "d2h_bytes_per_step": d2h / K,
+            "per_step": "advance one coarse step + FP64 mass/momentum of the finest level into a pinned host row "
+                        "(stream-ordered, no per-step synchronisation); initial fields H2D and final macros D2H "
+                        "amortised over the steps; no L2 flush between steps"}
+
+
+def bulk_at_scale(storage, flush):
+    """The 2-D bulk kernel on one large level (4096^2, 1.2 GB per launch in FP32),
+    where the launch is long enough for HBM to be the limit."""
+    import torch
+
+    from paper_2004_14887_gb300 import lbm
+    from paper_2004_14887_gb300 import workloads as W
+
+    n = 4096
+    ds = {"lattice": 9, "coarse_n": (n, n), "boxes": [], "nu0": 1e-5, "storage": storage,
+          "init": {"kind": "vortex", "xc": n / 2, "yc": n / 2, "Rc": n / 16, "swirl": 0.05, "U": (0.05, 0.02, 0.0)}}
+    hs = lbm.Hierarchy(ds)
+    r, u = W.init_fields(ds, 0)
+    hs.init_fields(0, r, u)
+    hs.autotune(reps=5)
+    hs.advance(3)
+    torch.cuda.synchronize()
+    ks = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    hs.advance(ks)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1) / ks
+    bytes_s = n * n * 2 * 9 * BYTES_PER_POP[storage]
+    hs.close()
+    return {"workload": f"single periodic D2Q9 level {n}^2, {storage}, vortex", "ms_per_launch": ms_s,
+            "achieved_gbs": bytes_s / (ms_s * 1e-3) / 1e9, "frac": bytes_s / (ms_s * 1e-3) / 1e9 / _peaks()[0],
+            "mlups": n * n / (ms_s * 1e-3) / 1e6}
+
+
+# the other configurations, each reported beside the headline with its own roofline:
+# (workload, storage, timed steps)
+EXTRAS = [("pulse2d_3lvl", "f32", 200), ("pulse2d_3lvl", "f16s_mean", 200), ("vortex3d_3lvl", "f32", 20),
+          ("batch2d", "f32", 20)]
+
+
+def run_gb300(args):
+    import torch
+
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     # one non-default stream for the library, the L2 flushes and the timing events
@@ -298,222 +493,77 @@ def run_gb300(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-
-            dist.barrier()
-
-    def max_over_ranks_gpu(x):
-        return max_over_ranks(x, device="cuda")
-
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
-
-    def make(storage, use_graphs=True):
-        d = _with_storage(WORKLOADS[args.workload](), storage)
-        tc = time.perf_counter()
-        h = lbm.Hierarchy(d, use_graphs=use_graphs)
-        print(f"[bench] {args.workload} {storage}: set-up {time.perf_counter() - tc:.2f} s, "
-              f"{h.device_bytes() / 1e9:.2f} GB on the device", file=sys.stderr, flush=True)
-        if not args.no_autotune:
-            res = h.autotune(reps=10)
-            print(f"[bench] autotuned tile shapes per level: {res['cfg']}", file=sys.stderr, flush=True)
-        for l in range(h.n_levels):
-            r, u = W.init_fields(d, l)
-            h.init_fields(l, r, u)
-        return d, h
-
-    def timed(h, K, Wm, sampler_dev=None):
-        h.advance(Wm)
-        torch.cuda.synchronize()
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-        n0 = h.launch_count()
-        barrier()
-        torch.cuda.synchronize()
-        clocks = None
-        t0 = time.perf_counter()
-        if sampler_dev is not None:
-            with ClockSampler(sampler_dev) as cs:
-                for k in range(K):
-                    flush.zero_()
-                    starts[k].record()
-                    h.advance(1)
-                    ends[k].record()
-                torch.cuda.synchronize()
-            clocks = cs.summary()
-        else:
-            for k in range(K):
-                flush.zero_()
-                starts[k].record()
-                h.advance(1)
-                ends[k].record()
-            torch.cuda.synchronize()
-        barrier()
-        wall = time.perf_counter() - t0
-        h.check_status()
-        dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-        return dev_ms, wall, h.launch_count() - n0, clocks
-
+    flush = _flush_buffer()
     K, Wm = args.steps, args.warmup
     main_storage = args.storage or DEFAULT_STORAGE[args.workload]
-    d, h = make(main_storage)
-    upd = W.updates_per_coarse_step(d)
-    feq = W.fine_equivalent_per_coarse_step(d)
-    dev_ms, wall, launches, clocks = timed(h, K, Wm, sampler_dev=local)
-    t = max_over_ranks_gpu(dev_ms) / 1e3
-    value = whole_job_rate(feq * K, ws, t) / 1e6
-    actual = whole_job_rate(upd * K, ws, t) / 1e6
+    if args.workload == "batch2d":
+        main = measure_batch(main_storage, K, Wm, flush, sampler_dev=local, ws=ws)
+    else:
+        main = measure_hierarchy(args.workload, main_storage, K, Wm, flush, sampler_dev=local,
+                                 autotune=not args.no_autotune, ws=ws)
 
-    # dominant kernel: the bulk collide-and-stream of the finest level (4 launches per step)
-    L = h.n_levels
-    h.timing_enable(True)
-    Kt = min(K, 200)
-    for _ in range(Kt):
-        flush.zero_()
-        h.advance(1)
-    ms, cnt = h.timing_read()
-    h.timing_enable(False)
-    bulk_ms = [m / max(c, 1) for m, c in zip(ms, cnt)]
-    nact = [h.levels[l]["n_active"] for l in range(L)]
-    bytes_finest = nact[L - 1] * 2 * h.q * BYTES_PER_POP[main_storage]
-    peak, peak_src = _peaks()
-    achieved = bytes_finest / (bulk_ms[L - 1] * 1e-3) / 1e9
-
-    # reduced / full precision variants on the same workload
+    # the other storage forms of the same workload (FP64 with few steps: it is the
+    # slow reference of the speed-up)
     variants = {}
-    if not args.no_variants:
+    if not args.no_variants and args.workload != "batch2d":
         for st in [x for x in ("f64", "f32", "f16s", "f16s_mean") if x != main_storage]:
-            dv, hv = make(st)
-            Kv = min(K, args.variant_steps if st == "f64" else K)
-            dms, _, _, _ = timed(hv, Kv, max(3, Wm // 2))
-            tv = max_over_ranks_gpu(dms) / 1e3
-            hv.timing_enable(True)
-            for _ in range(min(Kv, 100)):
-                flush.zero_()
-                hv.advance(1)
-            msv, cntv = hv.timing_read()
-            hv.timing_enable(False)
-            bl = msv[L - 1] / max(cntv[L - 1], 1)
-            variants[st] = {
-                "value": ws * feq * Kv / tv / 1e6, "actual_mlups": ws * upd * Kv / tv / 1e6,
-                "ms_per_step": 1e3 * tv / Kv, "steps": Kv,
-                "finest_bulk_gbs": nact[L - 1] * 2 * h.q * BYTES_PER_POP[st] / (bl * 1e-3) / 1e9,
-            }
-            hv.close()
-            del hv
-        vals = dict(variants)
-        vals[main_storage] = {"value": value}
+            Kv = min(K, args.variant_steps) if st == "f64" else K
+            v = measure_hierarchy(args.workload, st, Kv, min(Wm, 3), flush, autotune=not args.no_autotune, ws=ws,
+                                  timing_steps=min(Kv, 20))
+            variants[st] = {k: v[k] for k in ("value", "actual_mlups", "ms_per_step", "steps")}
+            variants[st]["finest_bulk_gbs"] = v["roofline"]["achieved"]
+            variants[st]["finest_bulk_frac"] = v["roofline"]["frac"]
+        vals = {k: v["value"] for k, v in variants.items()}
+        vals[main_storage] = main["value"]
         for st in ("f32", "f16s", "f16s_mean"):
             if st in vals and "f64" in vals:
-                variants[f"{st}_speedup_vs_f64"] = vals[st]["value"] / vals["f64"]["value"]
+                variants[f"{st}_speedup_vs_f64"] = vals[st] / vals["f64"]
 
-    # the same bulk kernel on one large level (4096^2, 1.2 GB per launch in FP32): where
-    # the step is long enough for HBM to be the limit, away from launch latency
-    scale = None
-    if not args.no_scale_check and L > 0 and h.q == 9:
-        n = 4096
-        ds = {"lattice": 9, "coarse_n": (n, n), "boxes": [], "nu0": 1e-5, "storage": main_storage,
-              "init": {"kind": "vortex", "xc": n / 2, "yc": n / 2, "Rc": n / 16, "swirl": 0.05, "U": (0.05, 0.02, 0.0)}}
-        hs = lbm.Hierarchy(ds)
-        r, u = W.init_fields(ds, 0)
-        hs.init_fields(0, r, u)
-        if not args.no_autotune:
-            hs.autotune(reps=5)
-        hs.advance(3)
-        torch.cuda.synchronize()
-        ks = 20
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        hs.advance(ks)
-        e1.record()
-        torch.cuda.synchronize()
-        ms_s = e0.elapsed_time(e1) / ks
-        bytes_s = n * n * 2 * h.q * BYTES_PER_POP[main_storage]
-        scale = {"workload": f"single periodic D2Q9 level {n}^2, {main_storage}, vortex", "ms_per_launch": ms_s,
-                 "achieved_gbs": bytes_s / (ms_s * 1e-3) / 1e9, "frac": bytes_s / (ms_s * 1e-3) / 1e9 / _peaks()[0],
-                 "mlups": n * n / (ms_s * 1e-3) / 1e6}
-        hs.close()
-        del hs
+    extras = {}
+    if not args.no_extras and ws == 1:
+        for wl, st, ke in EXTRAS:
+            if wl == args.workload and st == main_storage:
+                continue
+            key = f"{wl}_{st}"
+            if wl == "batch2d":
+                extras[key] = measure_batch(st, ke, 5, flush)
+            else:
+                extras[key] = measure_hierarchy(wl, st, ke, 5, flush, timing_steps=min(ke, 50))
+            extras[key]["workload"] = WORKLOAD_TEXT[wl] + f", {st} storage"
+        if not args.no_scale_check:
+            extras["bulk_at_scale_f32"] = bulk_at_scale("f32", flush)
+            extras["bulk_at_scale_f16s"] = bulk_at_scale("f16s", flush)
 
-    # end to end through the public API with host buffers: the initial fields from
-    # pinned host memory (H2D), then every step advances and copies the finest level's
-    # mass and momentum into its row of a pinned host array (D2H, lbm_reduce_async,
-    # stream-ordered), and at the end the macros of every level (D2H, synchronising);
-    # the handle is set up as a user would: created, initialised, autotuned
     e2e = None
-    if not args.no_e2e:
-        de = _with_storage(WORKLOADS[args.workload](), main_storage)
-        he = lbm.Hierarchy(de)
-        fields = []
-        for l in range(he.n_levels):
-            r, u = W.init_fields(de, l)
-            rp = torch.from_numpy(r).pin_memory().numpy()
-            up = torch.from_numpy(u).pin_memory().numpy()
-            fields.append((rp, up))
-            he.init_fields(l, rp, up)
-        if not args.no_autotune:
-            he.autotune(reps=10)
-        outs = [(torch.empty(he.levels[l]["N"], dtype=torch.float64).pin_memory().numpy(),
-                 torch.empty((he.D, he.levels[l]["N"]), dtype=torch.float64).pin_memory().numpy())
-                for l in range(he.n_levels)]
-        sums = torch.zeros((K, 4), dtype=torch.float64).pin_memory()
-        # warm-up on the workload's own state (graph capture); the timed region starts
-        # again from the initial fields
-        he.advance(3)
-        he.check_status()
-        torch.cuda.synchronize()
-        barrier()
-        te = time.perf_counter()
-        for l in range(he.n_levels):
-            he.init_fields(l, *fields[l])
-        for k in range(K):
-            he.advance(1)
-            he.reduce_async(he.n_levels - 1, sums[k])
-        for l in range(he.n_levels):
-            he.get_macros(l, out=outs[l])
-        torch.cuda.synchronize()
-        barrier()
-        tw = max_over_ranks_gpu(time.perf_counter() - te)
-        he.check_status()
-        if not bool(torch.isfinite(sums).all()):
-            raise RuntimeError("end-to-end run: non-finite mass or momentum")
-        h2d = sum(a.nbytes + b.nbytes for a, b in fields)
-        d2h = sum(a.nbytes + b.nbytes for a, b in outs) + sums.numel() * 8
-        e2e = {"value": ws * feq * K / tw / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
-               "d2h_bytes_per_step": d2h / K,
-               "per_step": "advance one coarse step + FP64 mass/momentum of the finest level into a pinned "
-                           "host row (stream-ordered, no per-step synchronisation); initial fields H2D and "
-                           "final macros D2H amortised over the steps; no L2 flush between steps"}
-        he.close()
+    if not args.no_e2e and args.workload != "batch2d":
+        e2e = measure_e2e(args.workload, main_storage, K, ws=ws)
 
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
-        "ms_per_step": 1e3 * t / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
+        "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": main_storage, "data": "synthetic (seeded analytic fields, no dataset)",
-        "config": {"workload": WORKLOAD_TEXT[args.workload] + f", {main_storage} storage", "levels": L,
-                   "node_updates_per_step": upd, "fine_equivalent_updates_per_step": feq,
-                   "active_nodes_per_level": nact, "l2": "flushed (256 MB write) before every timed step",
+        "config": {"workload": WORKLOAD_TEXT[args.workload] + f", {main_storage} storage",
+                   "node_updates_per_step": main["node_updates_per_step"],
+                   "fine_equivalent_updates_per_step": main["fine_equivalent_updates_per_step"],
+                   "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
-        "actual_mlups": actual,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": _traffic_from_profiles(args.workload, main_storage),
-                     "kernel": f"bulk collide-and-stream, finest level (level {L - 1})",
-                     "algorithmic_bytes_per_launch": bytes_finest, "avg_launch_ms": bulk_ms[L - 1],
-                     "peak_source": f"{peak_src} hbm_gbs"},
-        "bulk_ms_per_launch_by_level": bulk_ms,
-        "step_roofline_frac": (upd * 2 * h.q * BYTES_PER_POP[main_storage]) / (t / K) / 1e9 / peak,
-        "gpu_launches": launches,
-        "clocks": clocks,
+        "actual_mlups": main["actual_mlups"],
+        "roofline": main["roofline"],
+        "gpu_launches": main["gpu_launches"],
+        "clocks": main["clocks"],
         "e2e": e2e,
-        "variants": variants,
-        "bulk_at_scale": scale,
     }
-    h.close()
+    for k in ("active_nodes_per_level", "bulk_ms_per_launch_by_level", "step_roofline_frac", "tile_config_per_level",
+              "device_bytes", "setup_s", "hierarchies"):
+        if k in main:
+            line[k] = main[k]
+    line["variants"] = variants
+    line["extras"] = extras
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_steps)
-        line["accuracy"] = accuracy(args.workload, [main_storage] + [x for x in variants if "speedup" not in x])
+        line["cpu_baseline_all_cores"] = cpu_baseline(args.workload, args.cpu_steps, threaded=True)
+        forms = [main_storage] + [x for x in variants if "speedup" not in x]
+        line["accuracy"] = accuracy(args.workload, forms)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -523,25 +573,26 @@ def run_gb300(args):
 
 
 # Bounded samples for the oracle (CPU baseline, reference arm, accuracy): a replica of
-# each workload with the same proportions and physics, and the coarse steps that keep
-# the single-threaded oracle within ~10-30 s.
+# each workload with the same proportions and physics, the coarse steps that keep the
+# single-threaded oracle within ~10-30 s, and the steps of the accuracy comparison.
 REPLICA = {
     "pulse2d_3lvl": ("128^2 three-level replica (1/4 of each axis)", 150, 40),
     "vortex2d_2lvl": ("full-size 128^2 two-level hierarchy (no replica needed)", 150, 40),
     "vortex3d_3lvl": ("32^3 three-level replica (1/8 of each axis)", 15, 6),
     "vortex3d_3lvl_128": ("32^3 three-level replica (1/8 of vortex3d_3lvl per axis)", 15, 6),
-    "slab3d_3lvl": ("64x64x32 three-level replica (1/8 of each axis)", 3, 2),
+    "slab3d_3lvl": ("64x64x32 three-level replica (1/8 of each axis)", 4, 2),
+    "slab3d_3lvl_256": ("64x64x32 three-level replica (1/8 of slab3d_3lvl per axis)", 4, 2),
     "batch2d": ("one 128^2 two-level member", 150, 40),
 }
 
 
-def _replica_desc(workload="pulse2d_3lvl", storage="f64"):
+def _replica_desc(workload="slab3d_3lvl", storage="f64"):
     """The replica of a workload on which the oracle is timed and compared."""
     from paper_2004_14887_gb300 import workloads as W
 
     if workload in ("vortex3d_3lvl", "vortex3d_3lvl_128"):
         return W.vortex3d(n=32, boxes=((8, 24), (12, 20)), storage=storage)
-    if workload == "slab3d_3lvl":
+    if workload in ("slab3d_3lvl", "slab3d_3lvl_256"):
         return W.slab3d(nxy=64, nz=32, slab=(12, 20), box=((16, 16, 14), (48, 48, 18)), storage=storage)
     if workload == "vortex2d_2lvl":
         return W.vortex2d(storage=storage)
@@ -550,31 +601,39 @@ def _replica_desc(workload="pulse2d_3lvl", storage="f64"):
     return W.pulse2d(n=128, boxes=((32, 96), (48, 80)), steps=20, storage=storage)
 
 
-def _oracle_run(workload, steps, warm=1):
+def _oracle_run(d, steps, warm=1, threaded=False):
     from oracle import oracle as O
-    from paper_2004_14887_gb300 import workloads as W
 
-    d = _replica_desc(workload)
-    o = O.Hierarchy(d)
+    o = O.Hierarchy(d, threaded=threaded)
     for l in range(o.n_levels):
-        r, u = W.init_fields(d, l)
+        r, u = _fields(d, l)
         o.init(l, r, u)
     o.advance(warm)
     t0 = time.perf_counter()
     o.advance(steps)
-    return d, o, time.perf_counter() - t0
+    return o, time.perf_counter() - t0
 
 
-def cpu_baseline(workload, steps=None):
+def cpu_baseline(workload, steps=None, threaded=False):
+    """The FP64 oracle timed on the workload's replica: its plain build
+    (single-threaded), or with threaded=True its OpenMP build on every host core
+    (the same per-node arithmetic, the node loops shared out over threads)."""
     from paper_2004_14887_gb300 import workloads as W
 
     text, default_steps, _ = REPLICA[workload]
     steps = steps or default_steps
-    d, _, dt = _oracle_run(workload, steps)
+    cores = 1
+    if threaded:
+        from oracle import oracle as O
+
+        cores = O.threads(os.cpu_count() or 1)
+    d = _replica_desc(workload)
+    _, dt = _oracle_run(d, steps, threaded=threaded)
     feq = W.fine_equivalent_per_coarse_step(d)
-    return {"value": feq * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+    how = f"OpenMP FP64 oracle on {cores} host threads" if threaded else "single-threaded FP64 oracle"
+    return {"value": feq * steps / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{steps} coarse steps of the {text} of the workload "
-                      f"({W.updates_per_coarse_step(d)} node updates per step), single-threaded FP64 oracle",
+                      f"({W.updates_per_coarse_step(d)} node updates per step), {how}",
             "actual_mlups": W.updates_per_coarse_step(d) * steps / dt / 1e6}
 
 
@@ -591,89 +650,105 @@ def _db(p_pa):
     return 20.0 * math.log10(p_pa / P_DB_REF_PA) if p_pa > 0 else float("-inf")
 
 
-def _storage_error(d, st, steps, ref):
+def _storage_error(d, st, steps, o):
     """Advance description d in storage st on the GPU and compare every level with the
-    oracle's macros ref: (rel Linf rho, rel Linf u, max|drho|, sum drho^2, nodes,
-    max|rho - 1| of the oracle)."""
+    oracle o: (rel Linf rho, rel Linf u, max|drho|, volume-weighted sum drho^2, total
+    weight, max|rho - 1| of the oracle)."""
     import numpy as np
 
+    from oracle import oracle as O
     from paper_2004_14887_gb300 import lbm
-    from paper_2004_14887_gb300 import workloads as W
 
     d = _with_storage(d, st)
     g = lbm.Hierarchy(d)
     for l in range(g.n_levels):
-        r, u = W.init_fields(d, l)
+        r, u = _fields(d, l)
         g.init_fields(l, r, u)
     g.advance(steps)
     g.check_status()
     er = eu = ed = 0.0
-    sq, cnt, amp = 0.0, 0, 0.0
+    sq, wsum, amp = 0.0, 0.0, 0.0
+    L = g.n_levels - 1
     for l in range(g.n_levels):
-        m = g.node_class(l) != lbm.HOLE
+        m = o.node_class(l) != O.HOLE
         rg, ug = g.get_macros(l)
-        ro, uo = ref[l]
+        ro, uo = o.macros(l)
         amp = max(amp, float(np.max(np.abs(ro[m] - 1.0))))
         dr = rg[m] - ro[m]
         er = max(er, float(np.max(np.abs(dr)) / np.max(np.abs(ro[m]))))
         eu = max(eu, float(np.max(np.abs(ug[:, m] - uo[:, m])) / max(np.max(np.abs(uo[:, m])), 1e-300)))
         ed = max(ed, float(np.max(np.abs(dr))))
-        sq += float(np.sum(dr * dr))
-        cnt += int(m.sum())
+        wv = float(1 << (g.D * (L - l)))  # cell volume in finest-level cells
+        sq += wv * float(np.sum(dr * dr))
+        wsum += wv * dr.size
     g.close()
-    return er, eu, ed, sq, cnt, amp
+    return er, eu, ed, sq, wsum, amp
+
+
+def _all_fine(d):
+    """Uniform periodic grid at the finest spacing of d over the same domain (level 0
+    of the result has tau_L: nu = 2^L nu_0), with the same analytic fields; one of its
+    steps is one finest-level step of d."""
+    L = len(d["boxes"])
+    f = 1 << L
+    D = 2 if d["lattice"] == 9 else 3
+    u = dict(d)
+    u["boxes"] = []
+    u["coarse_n"] = tuple(int(c) * f for c in d["coarse_n"][:D])
+    u["nu0"] = d["nu0"] * f
+    ini = dict(d["init"])
+    for k in ("xc", "yc", "zc", "Rc"):
+        if k in ini:
+            ini[k] = ini[k] * f
+    u["init"] = ini
+    u["name"] = (d.get("name") or "replica") + "_all_fine"
+    return u, f
 
 
 def accuracy(workload, storages):
     """The workload's replica advanced on the GPU in each storage and by the FP64
     oracle for the same steps: per storage, the relative L-infinity errors of rho and
     u (worst level), the density error relative to the signal amplitude max|rho - 1|,
-    and the RMS density error as a pressure in Pa-equivalent and in dB.  The same
-    comparison on a uniform grid (the replica's level 0 with no refinement) gives the
-    storage's precision floor; floor_ratio = RMS error of the refined run / that
-    floor, about 1 when the interface adds no error of its own beyond the storage's."""
-    from oracle import oracle as O
-    from paper_2004_14887_gb300 import workloads as W
-
+    and the volume-weighted RMS density error as a pressure in Pa-equivalent and in dB.
+    The same comparison on an all-fine uniform grid at the finest spacing over the same
+    physical time (2^L steps per coarse step) gives the storage's own precision floor
+    without any interface; floor_ratio = RMS error of the refined run / that floor."""
     text, _, steps = REPLICA[workload]
-    d64, o, _ = _oracle_run(workload, steps, warm=0)
-    ref = [o.macros(l) for l in range(o.n_levels)]
-    du = dict(d64, boxes=[])
-    ou = O.Hierarchy(du)
-    r, u = W.init_fields(du, 0)
-    ou.init(0, r, u)
-    ou.advance(steps)
-    ref_u = [ou.macros(0)]
+    d64 = _replica_desc(workload)
+    o, _ = _oracle_run(d64, steps, warm=0, threaded=True)
+    du, f = _all_fine(d64)
+    ou, _ = _oracle_run(du, steps * f, warm=0, threaded=True)
     out = {}
     for st in storages:
-        er, eu, ed, sq, cnt, amp = _storage_error(d64, st, steps, ref)
-        _, _, _, squ, cntu, _ = _storage_error(du, st, steps, ref_u)
-        rms = (sq / max(cnt, 1)) ** 0.5
-        floor = (squ / max(cntu, 1)) ** 0.5
+        er, eu, ed, sq, wsum, amp = _storage_error(d64, st, steps, o)
+        _, _, _, squ, wsu, _ = _storage_error(du, st, steps * f, ou)
+        rms = (sq / max(wsum, 1)) ** 0.5
+        floor = (squ / max(wsu, 1)) ** 0.5
         out[st] = {"rho_rel_linf": er, "u_rel_linf": eu, "drho_rel_amplitude": ed / max(amp, 1e-300),
                    "dp_rms_pa": rms * P_REF_PA, "dp_rms_db": _db(rms * P_REF_PA), "dp_max_pa": ed * P_REF_PA,
                    "amplitude_pa": amp * P_REF_PA, "amplitude_db": _db(amp * P_REF_PA),
                    "floor_dp_rms_pa": floor * P_REF_PA,
                    "floor_ratio": rms / floor if floor > 0 else (0.0 if rms == 0 else float("inf"))}
     return {"vs": "FP64 oracle", "sample": f"{steps} coarse steps of the {text}",
-            "floor": "the same comparison on the replica's level 0 alone (uniform grid, no interface)",
+            "floor": f"the same comparison on an all-fine uniform grid at the finest spacing ({f}x each axis of "
+                     f"level 0), {steps * f} steps (the same physical time), against the all-fine oracle",
+            "rms": "volume-weighted over the active nodes of every level (weight: cell volume)",
             "db_ref_pa": P_DB_REF_PA, "by_storage": out}
 
 
 def run_reference(args):
-    """The reference arm: the FP64 CPU oracle timed on a bounded sample of the same
-    workload (its replica), on rank 0 only."""
+    """The reference arm: the FP64 CPU oracle as it stands (its plain,
+    single-threaded build) timed on a bounded sample of the same workload (its
+    replica), on rank 0 only."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     from paper_2004_14887_gb300 import workloads as W
 
-    text, cpu_steps, _ = REPLICA[args.workload]
-    # the oracle's steps are bounded so that the arm ends within minutes (3-D replicas
-    # take about a second per coarse step)
-    cap = 2000 if cpu_steps >= 100 else 2 * cpu_steps
-    K = min(args.steps, cap)
-    d, _, dt = _oracle_run(args.workload, K, warm=min(args.warmup, max(1, cap // 20)))
+    text, _, _ = REPLICA[args.workload]
+    K = args.steps
+    d = _replica_desc(args.workload)
+    _, dt = _oracle_run(d, K, warm=min(args.warmup, 2))
     feq = W.fine_equivalent_per_coarse_step(d)
     v = feq * K / dt / 1e6
     sample = f"{K} coarse steps of the {text} of the workload, single-threaded FP64 oracle"
@@ -689,14 +764,15 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="pulse2d_3lvl", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--storage", default=None, choices=["f64", "f32", "f16s", "f16s_mean"])
-    ap.add_argument("--variant-steps", type=int, default=400)
+    ap.add_argument("--variant-steps", type=int, default=5, help="timed steps of the FP64 variant")
     ap.add_argument("--cpu-steps", type=int, default=None, help="oracle steps of the CPU baseline (default per workload)")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other configurations")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
@@ -706,8 +782,6 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "batch2d":
-        run_batch(args)
     else:
         run_gb300(args)
 
