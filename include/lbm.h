@@ -150,7 +150,11 @@ LBM_API int lbm_get_pops(lbm_h h, int level, double *f_out, int on_device);
 /* FP64 volume-weighted mass and momentum of a level over its active nodes with the
  * dual-cell weights in level-0 cell volumes (outline nodes weigh the part of their
  * cell inside the level): out[0] = mass, out[1..3] = momentum.  Returns
- * LBM_ERR_DIVERGED if a NaN or Inf was met. */
+ * LBM_ERR_DIVERGED if a NaN or Inf was met.
+ * The NaN flag is sticky: a reduction that meets NaN or Inf records it in the handle's
+ * device status word, and the word is cleared only by lbm_check_status.  Until then
+ * every later lbm_reduce and lbm_reduce_static on the handle returns LBM_ERR_DIVERGED
+ * (out still receives the sums), whichever level was reduced. */
 LBM_API int lbm_reduce(lbm_h h, int level, double out[4]);
 
 /* Stream-ordered variant of lbm_reduce, for loops that read a diagnostic after every
@@ -163,7 +167,9 @@ LBM_API int lbm_reduce(lbm_h h, int level, double out[4]);
  *   - out holds the result once the stream has passed the copy (lbm_synchronize or
  *     any synchronising call); the caller owns out and keeps it alive until then.
  *   - NaN or Inf is not reported by the return value: the sums hold it, and the
- *     device status word records it (lbm_check_status returns LBM_ERR_DIVERGED).
+ *     device status word records it (lbm_check_status returns LBM_ERR_DIVERGED and
+ *     clears the word).  The record is sticky: until that lbm_check_status, every
+ *     lbm_reduce and lbm_reduce_static on the handle returns LBM_ERR_DIVERGED.
  *   - Calls on one handle are ordered; each writes only its own out. */
 LBM_API int lbm_reduce_async(lbm_h h, int level, double *out, int on_device);
 
@@ -178,13 +184,16 @@ LBM_API int lbm_reduce_async(lbm_h h, int level, double *out, int on_device);
  *   - Same inputs, output and weights as lbm_reduce; out is a host buffer of 4 doubles.
  *   - Levels with more than LBM_STATIC_REDUCE_PARTIALS x 2048 box nodes are rejected
  *     with LBM_ERR_ARG and a message naming the limit.
- *   - The handle's device must be the current device.  The first call on a device
+ *   - The handle's device (the device current at its creation) must be the current
+ *     device; otherwise the call returns LBM_ERR_ARG.  The first call on a device
  *     looks up the array's device address (cudaGetSymbolAddress) and caches it; make
  *     that first call before any stream capture on that device.
  *   - All calls share the one array: calls whose work overlaps on the GPU (two
  *     streams, or two host threads) race and may return wrong sums.  Each call
  *     overwrites every partial it reads, so nothing has to be cleared between calls.
- *   - Synchronises the handle's stream; returns LBM_ERR_DIVERGED on NaN or Inf. */
+ *   - Synchronises the handle's stream; returns LBM_ERR_DIVERGED on NaN or Inf, and,
+ *     like lbm_reduce, whenever the handle's sticky NaN record is set (cleared only by
+ *     lbm_check_status). */
 #define LBM_STATIC_REDUCE_PARTIALS 4096
 LBM_API int lbm_reduce_static(lbm_h h, int level, double out[4]);
 
@@ -260,6 +269,21 @@ LBM_API int lbm_get_tile_config(lbm_h h, int level, int *cfg);
  * drops the captured graphs.  Returns LBM_ERR_ARG for another mode, or for a batch
  * (a batch takes NODE for every member: its phases cover all members' interfaces). */
 LBM_API int lbm_set_interface_mapping(lbm_h h, int mode);
+
+/* Test hook of the bounded waits of the D3Q19 bulk kernel (the paper has no counterpart;
+ * failure detection of this library).  From the next lbm_advance on, every bulk launch
+ * of `level` runs with its device-side wait limit set to limit_us microseconds, and
+ * its block (bx, by, bz) of the launch grid (see lbm_query_level and the 32 x 8 column
+ * tiling; bz is the z chunk) does not issue the copies of the k-th plane stage of its
+ * z march.  That block's wait for them gives up after the limit, records
+ * LBM_ERR_TIMEOUT in the status word (read by lbm_check_status), waits for the copies
+ * it did issue and returns; the other blocks finish normally and the device context
+ * stays usable, but the level's state is then invalid (re-initialise it).  The
+ * withheld stage must be one the block loads (a plane of its chunk, or the plane on
+ * either side, that is not a hole of the level).  level < 0 turns the hook off.
+ * Drops the captured graphs.  Returns LBM_ERR_ARG for a D2Q9 hierarchy, a batch, or
+ * arguments out of range (limit_us in [1, 1e7]). */
+LBM_API int lbm_debug_withhold_copy(lbm_h h, int level, int bx, int by, int bz, int k, int64_t limit_us);
 
 /* Kernel timing: while enabled, lbm_advance launches eagerly and brackets every
  * bulk collide-and-stream launch with CUDA events on the handle's stream.

@@ -146,6 +146,12 @@ struct LevelDev {
     const int *ie_nst;
     const int *ie_st;
     const void *ie_w;  // [n_ie][16] stencil weights in the arithmetic type
+    // FP16-shifted storage (D3Q19 bulk kernel): moments of the shift s_i (sum s, sum c_a
+    // s, sum c_a c_b s in the order xx yy zz xy xz yz), and per opposite pair (i odd,
+    // opp(i) = i + 1) s_i = w_i (she_i + sho_i), s_opp(i) = w_i (she_i - sho_i); she_0 =
+    // s_0 / w_0
+    float smom[10];
+    float she[19], sho[19];
 };
 
 // wrap (periodic) or reject a coordinate; returns false outside a non-periodic box

@@ -19,6 +19,7 @@
 
 #include "../../include/lbm.h"
 #include "lbm_kernels.cuh"
+#include "lbm_bulk3d.cuh"
 
 using namespace lbmg;
 
@@ -86,6 +87,7 @@ struct lbm_hierarchy {
     Iface ifc[LBM_MAX_LEVELS];  // ifc[l] couples level l-1 and level l (l >= 1)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    int device = 0;  // the CUDA device current at creation; the handle's arrays live there
     // second stream: a level's TF-gradient / hanging-node launch runs beside its child
     // level's sub-steps (fork and join events per level; captured as graph branches)
     cudaStream_t side = nullptr;
@@ -98,6 +100,9 @@ struct lbm_hierarchy {
     int64_t device_bytes = 0;
     int *d_status = nullptr, *d_maxit = nullptr;
     int if_mode = LBM_IFACE_AUTO;  // interface thread mapping (lbm_set_interface_mapping)
+    // test hook of the 3-D bulk kernel's bounded waits (lbm_debug_withhold_copy)
+    int withhold_level = -1, withhold_block = -1, withhold_k = -1;
+    unsigned long long withhold_limit_ns = 0;
     float shift[19] = {};          // FP16-shifted storage: f_i - shift[i] (f_i^eq(1, u_shift))
     double *d_partial = nullptr, *d_red = nullptr;
     int red_blocks = 0;
@@ -890,6 +895,34 @@ LevelDev level_dev(const lbm_h h, int l)
     d.om = 1.0 - 1.0 / v.tau;
     d.sigma = h->d.sigma;
     d.spsi = (double)h->d.psi_sign;
+    // FP16 shift folded into the D3Q19 bulk kernel's moments and pair outputs
+    if (h->Q == 19) {
+        double sm[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int i = 0; i < 19; i++) {
+            const double si = (double)h->shift[i];
+            const int c0 = Lat<19>::c(i, 0), c1 = Lat<19>::c(i, 1), c2 = Lat<19>::c(i, 2);
+            sm[0] += si;
+            sm[1] += c0 * si;
+            sm[2] += c1 * si;
+            sm[3] += c2 * si;
+            sm[4] += c0 * c0 * si;
+            sm[5] += c1 * c1 * si;
+            sm[6] += c2 * c2 * si;
+            sm[7] += c0 * c1 * si;
+            sm[8] += c0 * c2 * si;
+            sm[9] += c1 * c2 * si;
+        }
+        for (int q = 0; q < 10; q++) d.smom[q] = (float)sm[q];
+        d.she[0] = (float)((double)h->shift[0] / Lat<19>::w(0));
+        d.sho[0] = 0.0f;
+        for (int i = 1; i < 19; i += 2) {
+            const double w = Lat<19>::w(i), sa = h->shift[i], sb = h->shift[i + 1];
+            d.she[i] = (float)((sa + sb) / (2.0 * w));
+            d.sho[i] = (float)((sa - sb) / (2.0 * w));
+            d.she[i + 1] = d.she[i];
+            d.sho[i + 1] = -d.sho[i];
+        }
+    }
     d.tauf = (float)d.tau;
     d.omf = (float)d.om;
     d.sigmaf = (float)d.sigma;
@@ -981,7 +1014,8 @@ struct Sched {
         else
             launch_chained(k_bulk3d<Q, S, T3X, T3Y>, nt, dim3(T3X * T3Y), Stage3<Q, S, T3X, T3Y>::smem_bytes, st,
                            v.tmap[src == v.f[0] ? 0 : 1], level_dev(h, l), (const S *)src, (S *)dst, tau, om, sig,
-                           sps, v.zc, h->d_status, kWaitLimitNs);
+                           sps, v.zc, h->d_status, h->withhold_level == l ? h->withhold_limit_ns : kWaitLimitNs,
+                           h->withhold_level == l ? h->withhold_block : -1, h->withhold_level == l ? h->withhold_k : -1);
         h->launch_counter++;
         if (h->timing) {
             cudaEventRecord(h->ev_pool[ev + 1], h->stream);
@@ -1218,6 +1252,10 @@ int lbm_create_hierarchy(const lbm_hierarchy_desc *desc, void *cuda_stream, lbm_
             delete h;
             return fail(nullptr, LBM_ERR_BAD_DESC, "level %d has more than 2^31 box nodes", l);
         }
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        delete h;
+        return fail(nullptr, LBM_ERR_CUDA, "cudaGetDevice failed");
+    }
     if (cuda_stream) {
         h->stream = (cudaStream_t)cuda_stream;
     } else {
@@ -1418,7 +1456,7 @@ int lbm_check_status(lbm_h h)
     int st = 0;
     CK(cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     CK(cudaMemset(h->d_status, 0, sizeof(int)));
-    if (st & ST_TIMEOUT) return fail(h, LBM_ERR_TIMEOUT, "a grid barrier wait gave up");
+    if (st & ST_TIMEOUT) return fail(h, LBM_ERR_TIMEOUT, "a bounded device-side wait gave up");
     if (st & ST_NEWTON) return fail(h, LBM_ERR_NEWTON, "Newton did not converge at a TF node");
     if (st & ST_NAN) return fail(h, LBM_ERR_DIVERGED, "NaN or Inf met");
     return LBM_OK;
@@ -1534,6 +1572,10 @@ extern "C" int lbm_reduce_static(lbm_h h, int level, double out[4])
                     "(use lbm_reduce)", level, v.N, (long long)kStaticPartials * kStaticNodesPerBlock);
     int dev = 0;
     CK(cudaGetDevice(&dev));
+    // the scratch address below is the current device's copy of the array: a handle
+    // of another device would get a pointer its kernels cannot use
+    if (dev != h->device)
+        return fail(h, LBM_ERR_ARG, "the handle lives on device %d but device %d is current", h->device, dev);
     if (dev < 0 || dev >= 256) return fail(h, LBM_ERR_ARG, "device ordinal %d out of range", dev);
     double *scratch;
     {
@@ -1729,6 +1771,10 @@ int lbm_create_batch(const lbm_hierarchy_desc *descs, int n, void *cuda_stream, 
     b->Q = 9;
     b->D = 2;
     b->nl = descs[0].n_levels;
+    if (cudaGetDevice(&b->device) != cudaSuccess) {
+        delete b;
+        return fail(nullptr, LBM_ERR_CUDA, "cudaGetDevice failed");
+    }
     if (cuda_stream) {
         b->stream = (cudaStream_t)cuda_stream;
     } else {
@@ -2001,6 +2047,30 @@ int lbm_set_tile_config(lbm_h h, int level, int cfg)
     }
     h->lev[level].tile_cfg = cfg;
     return h->D == 3 ? plan_chunks(h, level) : LBM_OK;
+}
+
+int lbm_debug_withhold_copy(lbm_h h, int level, int bx, int by, int bz, int k, int64_t limit_us)
+{
+    if (!h) return LBM_ERR_ARG;
+    if (h->batch || !h->members.empty()) return fail(h, LBM_ERR_ARG, "not for batches");
+    if (level < 0) {
+        h->withhold_level = h->withhold_block = h->withhold_k = -1;
+    } else {
+        if (!check_level(h, level)) return LBM_ERR_ARG;
+        const Level &v = h->lev[level];
+        if (h->Q != 19) return fail(h, LBM_ERR_ARG, "the staged bulk kernel is the D3Q19 one");
+        if (bx < 0 || by < 0 || bz < 0 || bx >= v.tiles[0] || by >= v.tiles[1] || bz >= v.tiles[2] || k < 0 ||
+            limit_us < 1 || limit_us > 10000000)
+            return fail(h, LBM_ERR_ARG, "block, stage or limit out of range");
+        h->withhold_level = level;
+        h->withhold_block = bx + v.tiles[0] * (by + v.tiles[1] * bz);
+        h->withhold_k = k;
+        h->withhold_limit_ns = (unsigned long long)limit_us * 1000ull;
+    }
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+    h->graph_launches.clear();
+    return LBM_OK;
 }
 
 int lbm_set_interface_mapping(lbm_h h, int mode)

@@ -1417,369 +1417,6 @@ __device__ __forceinline__ void load4d(void *dst, const CUtensorMap *map, unsign
 }
 }  // namespace tma
 
-// shapes of the 3-D staged kernel for storage S and a TX x TY column
-template <int Q, typename S, int TX, int TY>
-struct Stage3 {
-    using R = typename St<S>::R;
-    static constexpr int XA = 16 / (int)sizeof(S);   // x reach of the box below X0 (one 16-byte step)
-    static constexpr int BW = TX + 2 * XA;           // box: x in [X0-XA, X0+TX+XA), y in [Y0-2, Y0+TY+2)
-    static constexpr int BH = TY + 4;
-    static constexpr int BOX = BW * BH;               // elements of one population's box
-    static constexpr int HX = TX + 2, HY = TY + 2, HP = HX * HY;  // macro tile with its one-node halo
-    static constexpr int NRING = 4;                  // macro planes p-2 .. p+1 (one barrier per plane)
-    static constexpr size_t stage_bytes = (size_t)Q * BOX * sizeof(S);
-    static constexpr size_t ring_bytes = (size_t)NRING * 4 * HP * sizeof(R);
-    static constexpr size_t smem_bytes = 128 + 2 * stage_bytes + ring_bytes + 16;  // +128: alignment of the base
-    static_assert((BOX * sizeof(S)) % 128 == 0, "population boxes stay 128-byte aligned");
-    static_assert(BW <= 256 && BH <= 256, "tensor box limits");
-};
-
-// 3-D z-marching bulk kernel with staged planes.  One CTA per TX x TY column of nodes
-// and chunk of planes [zb, ze).  For each plane p the populations that stream into it
-// (population i from plane p - c_iz, over the column grown by XA nodes in x and 2 in
-// y) arrive in a shared-memory stage by bulk tensor copies (or, for a column that
-// meets a periodic seam in x or y, by plain loads with wrapped coordinates), one plane
-// ahead of the plane being used, in a ring of two stages with an mbarrier each.  From
-// a stage every thread pulls its node's populations (kept in registers for the next
-// step) and the macros of its node and of at most one halo node (written to a 4-plane
-// macro ring); the node of the plane below then collides with centred differences
-// taken from the ring.  Waits are bounded: on time-out the kernel sets ST_TIMEOUT,
-// waits (bounded) for its copies in flight and returns.
-template <int Q, typename S, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
-    k_bulk3d(const __grid_constant__ CUtensorMap tmap, LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
-             typename St<S>::R tau, typename St<S>::R om, typename St<S>::R sigma, typename St<S>::R spsi, int zc,
-             int *status, unsigned long long limit_ns)
-{
-    pdl_enter();
-    using L = Lat<Q>;
-    using G = Stage3<Q, S, TX, TY>;
-    using R = typename St<S>::R;
-    constexpr int D = 3;
-    static_assert(L::D == 3, "3-D kernel");
-    constexpr int XA = G::XA, BW = G::BW, BOX = G::BOX, HX = G::HX, HP = G::HP, NT = TX * TY;
-    constexpr int NB = 2 * HX + 2 * TY;
-    static_assert(NB <= NT, "one halo node per thread at most");
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char *base = smem_raw + ((128u - (tma::saddr(smem_raw) & 127u)) & 127u);  // 128-byte aligned stages
-    auto stage = [&](int s) { return (S *)(base + (size_t)s * G::stage_bytes); };
-    R *s_rho = (R *)(base + 2 * G::stage_bytes);  // [NRING][HP]
-    R *s_u = s_rho + G::NRING * HP;               // [NRING][3][HP]
-    unsigned long long *bar = (unsigned long long *)(base + 2 * G::stage_bytes + G::ring_bytes);
-
-    const LevelGeo &g = Lv.g;
-    const int X0 = blockIdx.x * TX, Y0 = blockIdx.y * TY;
-    const int zb = blockIdx.z * zc, ze = min(zb + zc, g.n[2]);
-    if (zb >= ze) return;
-    const int tid = threadIdx.x;
-    const int tx = tid % TX, ty = tid / TX;
-    const int x = X0 + tx, y = Y0 + ty;
-    const bool in_xy = x < g.n[0] && y < g.n[1];
-    const int hs = (tx + 1) + HX * (ty + 1);
-    // halo nodes are dealt out to every warp (node w + NW * lane of warp w), so that no
-    // warp reaches the per-plane barrier late
-    constexpr int NW = NT / 32;
-    const int hn = (tid >> 5) + NW * (tid & 31);
-    int hb = -1, hx = 0, hy = 0;
-    if (hn < NB) {
-        if (hn < HX) {
-            hx = hn;
-            hy = 0;
-        } else if (hn < 2 * HX) {
-            hx = hn - HX;
-            hy = TY + 1;
-        } else {
-            const int b = hn - 2 * HX;
-            hy = 1 + (b >> 1);
-            hx = (b & 1) ? HX - 1 : 0;
-        }
-        hb = hx + HX * hy;
-    }
-    const bool issuer = tid == NT - 32;  // lane 0 of the last warp issues the tensor copies
-    // own node and halo node in box coordinates (bx, by) of a stage
-    const int own_b = (ty + 2) * BW + (tx + XA);
-    const int halo_b = (hy + 1) * BW + (hx - 1 + XA);
-    const int n01 = g.px * g.n[1];
-    // a column whose stage would cross a periodic seam in x or y is filled by plain loads
-    const bool seam = (g.per[0] && (X0 - 2 < 0 || X0 + TX + 1 > g.n[0] - 1)) ||
-                      (g.per[1] && (Y0 - 2 < 0 || Y0 + TY + 1 > g.n[1] - 1));
-    // seam stages in 16-byte chunks when a periodic x extent is whole chunks, else by
-    // elements; both asynchronous except element copies of 2-byte storage
-    const bool chunked = !g.per[0] || g.n[0] % (16 / (int)sizeof(S)) == 0;
-    const bool async_fill = chunked || sizeof(S) >= 4;
-
-    // seam columns: the box elements a thread copies are the same in every plane;
-    // their wrapped x-y slot offsets (-1: off a non-periodic box) are fixed here
-    constexpr int NJ = (BOX + NT - 1) / NT;
-    int xy_off[NJ];
-#pragma unroll
-    for (int j = 0; j < NJ; j++) {
-        const int e = tid + j * NT;
-        int sx = X0 - XA + e % BW, sy = Y0 - 2 + e / BW;
-        const bool ok = e < BOX && wrap_coord(sx, g.n[0], g.per[0]) && wrap_coord(sy, g.n[1], g.per[1]);
-        xy_off[j] = ok ? sx + g.px * sy : -1;
-    }
-    if (issuer) {
-        tma::mbar_init(&bar[0], 1);
-        tma::mbar_init(&bar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-
-    const int K = ze - zb + 2;  // planes zb-1 .. ze: macros of all, collisions of zb .. ze-1
-    // class of plane k: a plane off a non-periodic box counts as a hole plane (no stage)
-    auto plane_of = [&](int k) { return zb - 1 + k; };
-    auto class_of = [&](int k) {
-        const int p = plane_of(k);
-        if (!g.per[2] && (p < 0 || p >= g.n[2])) return (int)LOAD_HOLE;
-        return plane_class(Lv, X0, Y0, TX, TY, p);
-    };
-    unsigned phase = 0u, pending = 0u;  // per stage: parity of the next wait, copy in flight
-    auto issue = [&](int k, int cls_k) {
-        if (cls_k == LOAD_HOLE) return;
-        const int s = k & 1, p = plane_of(k);
-        S *dst = stage(s);
-        if (!seam) {
-            if (issuer) {
-                tma::fence_proxy_async();
-                tma::mbar_expect_tx(&bar[s], (unsigned)G::stage_bytes);
-                static_for<Q>([&](auto ic) {
-                    constexpr int i = decltype(ic)::value;
-                    int zq = p - L::c(i, 2);
-                    if (g.per[2]) zq = zq < 0 ? zq + g.n[2] : (zq >= g.n[2] ? zq - g.n[2] : zq);
-                    tma::load4d(dst + i * BOX, &tmap, &bar[s], X0 - XA, Y0 - 2, zq, i);
-                });
-            }
-            pending |= 1u << s;
-        } else if (chunked) {
-            // 16-byte asynchronous copies with wrapped coordinates: a box row is whole
-            // 16-byte chunks, and with a periodic x extent of whole chunks a chunk never
-            // straddles the seam (completed before the barrier that precedes the use)
-            int zo[3];  // slot offset of planes p+1, p, p-1 (c_z = -1, 0, 1); -1 off the box
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                int sz = p + 1 - c;
-                zo[c] = wrap_coord(sz, g.n[2], g.per[2]) ? n01 * sz : -1;
-            }
-            constexpr int CE = 16 / (int)sizeof(S), CPR = BW / CE, NCH = CPR * G::BH;
-            static_assert(BW % CE == 0 && NCH <= NT, "one chunk per thread and population");
-            if (tid < NCH) {
-                const int row = tid / CPR, cc = tid % CPR;
-                int sx = X0 - XA + cc * CE, sy = Y0 - 2 + row;
-                // off a non-periodic x extent: a chunk that starts inside the row ends
-                // inside its padded pitch (px is a multiple of 8 nodes)
-                const bool okxy = wrap_coord(sy, g.n[1], g.per[1]) &&
-                                  (g.per[0] ? wrap_coord(sx, g.n[0], 1) : (sx >= 0 && sx < g.n[0]));
-                const int oxy = okxy ? sx + g.px * sy : 0;
-                static_for<Q>([&](auto ic) {
-                    constexpr int i = decltype(ic)::value;
-                    const int z0 = zo[L::c(i, 2) + 1];
-                    const bool ok = okxy && z0 >= 0;
-                    tma::cp_async<16>(dst + i * BOX + row * BW + cc * CE,
-                                      fsrc + (long long)i * g.pitch + (ok ? oxy + z0 : 0), ok);
-                });
-            }
-            tma::cp_async_commit();
-        } else {
-            // element copies with wrapped coordinates (asynchronous for 4- and 8-byte
-            // types; completed before the barrier that precedes the stage's use)
-            int zo[3];  // slot offset of planes p+1, p, p-1 (c_z = -1, 0, 1); -1 off the box
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                int sz = p + 1 - c;
-                zo[c] = wrap_coord(sz, g.n[2], g.per[2]) ? n01 * sz : -1;
-            }
-            static_for<Q>([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                const S *src = fsrc + (long long)i * g.pitch;
-                const int z0 = zo[L::c(i, 2) + 1];
-#pragma unroll
-                for (int j = 0; j < NJ; j++) {
-                    const int e = tid + j * NT;
-                    if (e >= BOX) break;
-                    const bool ok = xy_off[j] >= 0 && z0 >= 0;
-                    if constexpr (sizeof(S) >= 4)
-                        tma::cp_async<(int)sizeof(S)>(dst + i * BOX + e, ok ? src + xy_off[j] + z0 : src, ok);
-                    else
-                        dst[i * BOX + e] = ok ? src[xy_off[j] + z0] : S();
-                }
-            });
-            if constexpr (sizeof(S) >= 4) tma::cp_async_commit();
-        }
-    };
-
-    // tags of the own and halo node of plane k (general planes only)
-    auto tags_of = [&](int k, int &t_own, int &t_halo) {
-        const int p = plane_of(k);
-        int ox = x, oy = y, oz = p;
-        const bool ok = wrap_coord(ox, g.n[0], g.per[0]) && wrap_coord(oy, g.n[1], g.per[1]) &&
-                        wrap_coord(oz, g.n[2], g.per[2]);
-        t_own = ok ? Lv.tag[box_index(g, ox, oy, oz)] : TAG_HOLE;
-        t_halo = TAG_HOLE;
-        if (hb >= 0) {
-            int qx = X0 + hx - 1, qy = Y0 + hy - 1, qz = p;
-            const bool hok = wrap_coord(qx, g.n[0], g.per[0]) && wrap_coord(qy, g.n[1], g.per[1]) &&
-                             wrap_coord(qz, g.n[2], g.per[2]);
-            t_halo = hok ? Lv.tag[box_index(g, qx, qy, qz)] : TAG_HOLE;
-        }
-    };
-
-    R fc[Q], fn[Q];
-    int tc = TAG_HOLE, tn = TAG_HOLE;
-    int nt_own = TAG_HOLE, nt_halo = TAG_HOLE;  // tags of the next general plane (loaded one plane ahead)
-    int c0 = class_of(0), c1 = class_of(1);  // classes of planes k, k + 1 (K >= 3)
-    issue(0, c0);
-    issue(1, c1);
-    if (seam) {  // stages filled by copies from the threads
-        if (async_fill) tma::cp_async_wait_all();
-        __syncthreads();
-    }
-    if (c0 == LOAD_GENERAL) tags_of(0, nt_own, nt_halo);
-    for (int k = 0; k < K; k++) {
-        const int p = plane_of(k);
-        const int s = k & 1;
-        const int cls = c0;
-        const int t_own = cls == LOAD_FAST ? TAG_BULK : nt_own, t_halo = cls == LOAD_FAST ? TAG_BULK : nt_halo;
-        if (k + 1 < K && c1 == LOAD_GENERAL) tags_of(k + 1, nt_own, nt_halo);
-        bool ok = true;
-        if (cls != LOAD_HOLE && !seam) {
-            ok = tma::mbar_wait(&bar[s], (phase >> s) & 1u, limit_ns);
-            phase ^= 1u << s;
-            if (ok) pending &= ~(1u << s);
-        }
-        // pull plane p from the stage: own node (kept) and halo node (macros only)
-        const int slot = p & (G::NRING - 1);
-        R r = R(1), u[3] = {R(0), R(0), R(0)};
-        tn = TAG_HOLE;
-        if (cls != LOAD_HOLE && ok) {
-            const S *st = stage(s);
-            tn = t_own;
-            if (tn == TAG_BULK) {
-                static_for<Q>([&](auto ic) {
-                    constexpr int i = decltype(ic)::value;
-                    fn[i] = St<S>::ld(st, i * BOX + own_b - L::c(i, 1) * BW - L::c(i, 0), g.shift[i]);
-                });
-                reg_moments<Q, R>(fn, r, u);
-            } else if (tn >= 0) {
-                const R *pop = (const R *)Lv.if_pop, *mac = (const R *)Lv.if_mac;
-#pragma unroll
-                for (int i = 0; i < Q; i++) fn[i] = pop[(long long)i * Lv.nif + tn];
-                r = mac[tn];
-#pragma unroll
-                for (int a = 0; a < D; a++) u[a] = mac[(long long)(1 + a) * Lv.nif + tn];
-            }
-        }
-        s_rho[slot * HP + hs] = r;
-#pragma unroll
-        for (int a = 0; a < D; a++) s_u[(slot * 3 + a) * HP + hs] = u[a];
-        if (hb >= 0) {
-            R hr = R(1), hu[3] = {R(0), R(0), R(0)};
-            if (cls != LOAD_HOLE && ok) {
-                if (t_halo == TAG_BULK) {
-                    const S *st = stage(s);
-                    R m0 = R(0), m1 = R(0), m2 = R(0), m3 = R(0);
-                    static_for<Q>([&](auto ic) {
-                        constexpr int i = decltype(ic)::value;
-                        const R v = St<S>::ld(st, i * BOX + halo_b - L::c(i, 1) * BW - L::c(i, 0), g.shift[i]);
-                        m0 += v;
-                        if constexpr (L::c(i, 0) > 0) m1 += v;
-                        else if constexpr (L::c(i, 0) < 0) m1 -= v;
-                        if constexpr (L::c(i, 1) > 0) m2 += v;
-                        else if constexpr (L::c(i, 1) < 0) m2 -= v;
-                        if constexpr (L::c(i, 2) > 0) m3 += v;
-                        else if constexpr (L::c(i, 2) < 0) m3 -= v;
-                    });
-                    const R ir = recip(m0);
-                    hr = m0;
-                    hu[0] = m1 * ir;
-                    hu[1] = m2 * ir;
-                    hu[2] = m3 * ir;
-                } else if (t_halo >= 0) {
-                    const R *mac = (const R *)Lv.if_mac;
-                    hr = mac[t_halo];
-#pragma unroll
-                    for (int a = 0; a < D; a++) hu[a] = mac[(long long)(1 + a) * Lv.nif + t_halo];
-                }
-            }
-            s_rho[slot * HP + hb] = hr;
-#pragma unroll
-            for (int a = 0; a < D; a++) s_u[(slot * 3 + a) * HP + hb] = hu[a];
-        }
-        if (!in_xy) tn = TAG_HOLE;  // a position past a periodic seam only feeds the halo
-        if (seam && async_fill) tma::cp_async_wait_all();  // the copies of the next stage, issued one plane ago
-        if (__syncthreads_or(!ok)) {
-            // a copy did not arrive in time: report, drain what is in flight, stop
-            if (tid == 0) atomicOr(status, ST_TIMEOUT);
-            for (int q = 0; q < 2; q++)
-                if ((pending >> q) & 1u) tma::mbar_wait(&bar[q], (phase >> q) & 1u, limit_ns);
-            return;
-        }
-        const int c2 = k + 2 < K ? class_of(k + 2) : (int)LOAD_HOLE;
-        if (k + 2 < K) issue(k + 2, c2);  // into the stage just read
-        c0 = c1;
-        c1 = c2;
-        // collide plane p - 1 with the macros of planes p - 2, p - 1, p
-        if (k >= 2 && tc != TAG_HOLE) {
-            const int z = p - 1;
-            const int sm = (z - 1) & (G::NRING - 1), s0 = z & (G::NRING - 1), sp = p & (G::NRING - 1);
-            R Sv[6], Cv[6];
-            const int idx = x + g.px * y + n01 * z;
-            if (tc == TAG_BULK) {
-                R nr[3][2], nu[3][2][3];
-                const int hh[2][2] = {{hs + 1, hs - 1}, {hs + HX, hs - HX}};
-#pragma unroll
-                for (int b = 0; b < 2; b++)
-#pragma unroll
-                    for (int s2 = 0; s2 < 2; s2++) {
-                        nr[b][s2] = s_rho[s0 * HP + hh[b][s2]];
-#pragma unroll
-                        for (int a = 0; a < 3; a++) nu[b][s2][a] = s_u[(s0 * 3 + a) * HP + hh[b][s2]];
-                    }
-                nr[2][0] = s_rho[sp * HP + hs];
-                nr[2][1] = s_rho[sm * HP + hs];
-#pragma unroll
-                for (int a = 0; a < 3; a++) {
-                    nu[2][0][a] = s_u[(sp * 3 + a) * HP + hs];
-                    nu[2][1][a] = s_u[(sm * 3 + a) * HP + hs];
-                }
-                fd_gradients<D, R>(nr, nu, R(0.5), Sv, Cv);
-            } else {
-                const R *tS = (const R *)Lv.if_S, *tC = (const R *)Lv.if_C;
-                if (tc >= Lv.ie_base && tc < Lv.ie_base + Lv.n_ie) {
-                    const int e = tc - Lv.ie_base, nst = Lv.ie_nst[e];
-#pragma unroll
-                    for (int q = 0; q < 6; q++) Sv[q] = Cv[q] = R(0);
-                    for (int j = 0; j < nst; j++) {
-                        const int tf = Lv.ie_st[e * 16 + j];
-                        const R wj = ((const R *)Lv.ie_w)[e * 16 + j];
-#pragma unroll
-                        for (int q = 0; q < 6; q++) {
-                            Sv[q] += wj * tS[(long long)q * Lv.nif + tf];
-                            Cv[q] += wj * tC[(long long)q * Lv.nif + tf];
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 6; q++) {
-                        Sv[q] = tS[(long long)q * Lv.nif + tc];
-                        Cv[q] = tC[(long long)q * Lv.nif + tc];
-                    }
-                }
-            }
-            R rho = s_rho[s0 * HP + hs], uc[3] = {s_u[(s0 * 3) * HP + hs], s_u[(s0 * 3 + 1) * HP + hs],
-                                                  s_u[(s0 * 3 + 2) * HP + hs]};
-            hrr_collide<Q, R>(fc, rho, uc, Sv, Cv, tau, om, sigma, spsi);
-            static_for<Q>([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                St<S>::st(fdst + (long long)i * g.pitch, idx, fc[i], g.shift[i]);
-            });
-        }
-#pragma unroll
-        for (int i = 0; i < Q; i++) fc[i] = fn[i];
-        tc = tn;
-    }
-}
-
 // ------------------------------------------------------------------ batched persistent launch
 // Many independent hierarchies with the same number of levels advance together: the
 // sub-cycle schedule of one coarse step is a list of phases (history + Newton,
@@ -2043,6 +1680,31 @@ __global__ void k_macros(LevelGeo g, const int *__restrict__ tag, const S *__res
         for (int a = 0; a < D; a++) u[(long long)a * g.N + idx] = hole ? 0.0 : m[a] / r;
 }
 
+// Sum of acc[0..3] over a block of 256 threads: warp shuffles within each warp, then
+// the first warp over the 8 warp sums; the result is valid in thread 0 (fixed order,
+// deterministic).
+__device__ __forceinline__ void block_sum4_256(double (&acc)[4])
+{
+    __shared__ double sw[4][8];
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 4; k++) sw[k][warp] = acc[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            acc[k] = lane < 8 ? sw[k][lane] : 0.0;
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+        }
+    }
+}
+
 // Volume-weighted mass and momentum, per-block FP64 partials (deterministic order)
 template <int Q, typename S>
 __global__ void k_reduce_partial(LevelGeo g, const int *__restrict__ tag, const S *__restrict__ f,
@@ -2050,7 +1712,6 @@ __global__ void k_reduce_partial(LevelGeo g, const int *__restrict__ tag, const 
 {
     using L = Lat<Q>;
     constexpr int D = L::D;
-    __shared__ double sh[4][256];
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     bool bad = false;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.N;
@@ -2067,32 +1728,19 @@ __global__ void k_reduce_partial(LevelGeo g, const int *__restrict__ tag, const 
         }
     }
     if (bad) atomicOr(status, ST_NAN);
-    for (int k = 0; k < 4; k++) sh[k][threadIdx.x] = acc[k];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            for (int k = 0; k < 4; k++) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
-        __syncthreads();
-    }
+    block_sum4_256(acc);
     if (threadIdx.x == 0)
-        for (int k = 0; k < 4; k++) partial[(long long)blockIdx.x * 4 + k] = sh[k][0];
+        for (int k = 0; k < 4; k++) partial[(long long)blockIdx.x * 4 + k] = acc[k];
 }
 
 __global__ void k_reduce_final(const double *__restrict__ partial, int nblocks, double *__restrict__ out)
 {
-    __shared__ double sh[4][256];
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
         for (int k = 0; k < 4; k++) acc[k] += partial[(long long)b * 4 + k];
-    for (int k = 0; k < 4; k++) sh[k][threadIdx.x] = acc[k];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            for (int k = 0; k < 4; k++) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
-        __syncthreads();
-    }
+    block_sum4_256(acc);
     if (threadIdx.x == 0)
-        for (int k = 0; k < 4; k++) out[k] = sh[k][0];
+        for (int k = 0; k < 4; k++) out[k] = acc[k];
 }
 
 }  // namespace lbmg

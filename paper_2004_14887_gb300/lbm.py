@@ -60,7 +60,7 @@ EXPORTS = [
     "lbm_last_error", "lbm_destroy", "lbm_reduce_static", "lbm_create_batch", "lbm_batch_member",
     "lbm_batch_check_barrier", "lbm_set_probes", "lbm_get_probes", "lbm_save_state", "lbm_load_state",
     "lbm_autotune", "lbm_set_tile_config", "lbm_get_tile_config", "lbm_set_interface_mapping",
-    "lbm_reduce_async",
+    "lbm_reduce_async", "lbm_debug_withhold_copy",
 ]
 TILE_CONFIGS = 5
 IFACE_AUTO, IFACE_NODE, IFACE_SEGMENT = 0, 1, 2
@@ -113,6 +113,7 @@ def lib():
     L.lbm_set_tile_config.argtypes = [vp, C.c_int, C.c_int]
     L.lbm_set_interface_mapping.argtypes = [vp, C.c_int]
     L.lbm_get_tile_config.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
+    L.lbm_debug_withhold_copy.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64]
     _lib = L
     return L
 
@@ -372,6 +373,14 @@ class Hierarchy:
                 json.dump(table, fh)
             os.replace(tmp, cache)
         return res
+
+    def debug_withhold_copy(self, level, block, k, limit_us):
+        """Test hook of the D3Q19 bulk kernel's bounded waits (lbm_debug_withhold_copy):
+        block (bx, by, bz) of the level's bulk launches leaves its k-th stage unfilled;
+        level < 0 turns it off."""
+        bx, by, bz = block
+        self._check(lib().lbm_debug_withhold_copy(self._h, int(level), int(bx), int(by), int(bz), int(k),
+                                                  int(limit_us)))
 
     def max_newton_iters(self):
         return lib().lbm_max_newton_iters(self._h)
