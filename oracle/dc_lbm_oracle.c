@@ -469,6 +469,82 @@ static long node_at(const orc_h *h, int l, const long *p)
     return idx;
 }
 
+/* Refined region of level l (l >= 1), in cells of its parent level l-1 given by their
+ * lower corner c (global level-(l-1) coordinates): the cells of the box [lo, hi)
+ * (level-0 cell units, times 2^(l-1)), all of them on an axis the level spans, and of
+ * those the ones the mask marks. */
+static int cell_refined(const orc_h *h, int l, const long *c)
+{
+    const orc_desc *d = &h->d;
+    const level_t *pv = &h->lev[l - 1];
+    long q[3];
+    long ext[3] = {1, 1, 1};
+    for (int a = 0; a < 3; a++) {
+        if (a >= h->L.D) {
+            q[a] = 0;
+            continue;
+        }
+        long ca = c[a];
+        if (pv->periodic[a]) ca = pv->off[a] + mod_l(ca - pv->off[a], pv->n[a]);
+        if (h->lev[l].periodic[a]) { /* spans the axis */
+            q[a] = 0;
+            continue;
+        }
+        long psc = 1L << (l - 1);
+        long lo = d->box_lo[l][a] * psc, hi = d->box_hi[l][a] * psc;
+        if (ca < lo || ca >= hi) return 0;
+        q[a] = ca - lo;
+        ext[a] = hi - lo;
+    }
+    if (!d->mask[l]) return 1;
+    return d->mask[l][q[0] + ext[0] * (q[1] + ext[1] * q[2])] != 0;
+}
+
+/* number of the 2^D cells around level-(l-1) node p that level l refines, and 2^D */
+static int refined_cells_around(const orc_h *h, int l, const long *p, int *total)
+{
+    int D = h->L.D, cnt = 0, tot = 0;
+    for (int k = 0; k < (1 << D); k++) {
+        long c[3] = {p[0], p[1], p[2]};
+        for (int a = 0; a < D; a++) c[a] -= (k >> a) & 1;
+        cnt += cell_refined(h, l, c);
+        tot++;
+    }
+    *total = tot;
+    return cnt;
+}
+
+/* level-l node p (l >= 1): number of parent cells it touches (the node lies on their
+ * closure) that level l refines, and how many it touches */
+static int refined_parent_cells_of_fine(const orc_h *h, int l, const long *p, int *total)
+{
+    int D = h->L.D, cnt = 0, tot = 0;
+    long opts[3][2];
+    int no[3];
+    for (int a = 0; a < 3; a++) {
+        if (a >= D) {
+            opts[a][0] = 0;
+            no[a] = 1;
+        } else if (mod_l(p[a], 2) == 0) {
+            opts[a][0] = p[a] / 2 - 1;
+            opts[a][1] = p[a] / 2;
+            no[a] = 2;
+        } else {
+            opts[a][0] = (p[a] - 1) / 2;
+            no[a] = 1;
+        }
+    }
+    for (int i0 = 0; i0 < no[0]; i0++)
+        for (int i1 = 0; i1 < no[1]; i1++)
+            for (int i2 = 0; i2 < no[2]; i2++) {
+                long c[3] = {opts[0][i0], opts[1][i1], opts[2][i2]};
+                cnt += cell_refined(h, l, c);
+                tot++;
+            }
+    *total = tot;
+    return cnt;
+}
+
 static void coords_of(const level_t *v, long idx, long *p)
 {
     long q0 = idx % v->n[0];
@@ -562,6 +638,24 @@ orc_h *orc_create(const orc_desc *d, char *err, int errlen)
         v->N = v->n[0] * v->n[1] * v->n[2];
         v->tau = l == 0 ? 0.5 + d->nu0 / CS2 : 2.0 * h->lev[l - 1].tau - 0.5; /* Eqs. linkTauNu, rescTau */
     }
+    /* staircase regions (masks): 2-D, finest level, no spanned axis, and no two refined
+     * cells that meet at a corner only (the interface stays a simple curve) */
+    for (int l = 1; l < h->nl; l++) {
+        if (!d->mask[l]) continue;
+        if (D != 2) FAIL("refinement masks are 2-D only");
+        if (l + 1 < h->nl) FAIL("a refinement mask is allowed on the finest level only");
+        for (int a = 0; a < D; a++)
+            if (h->lev[l].periodic[a]) FAIL("a masked level spans no axis");
+        long psc = 1L << (l - 1);
+        for (long cy = d->box_lo[l][1] * psc; cy <= d->box_hi[l][1] * psc; cy++)
+            for (long cx = d->box_lo[l][0] * psc; cx <= d->box_hi[l][0] * psc; cx++) {
+                long c00[3] = {cx - 1, cy - 1, 0}, c10[3] = {cx, cy - 1, 0}, c01[3] = {cx - 1, cy, 0},
+                     c11[3] = {cx, cy, 0};
+                int a00 = cell_refined(h, l, c00), a10 = cell_refined(h, l, c10), a01 = cell_refined(h, l, c01),
+                    a11 = cell_refined(h, l, c11);
+                if (a00 == a11 && a10 == a01 && a00 != a10) FAIL("two refined cells meet at a corner only");
+            }
+    }
     /* node classes */
     for (int l = 0; l < h->nl; l++) {
         level_t *v = &h->lev[l];
@@ -569,25 +663,26 @@ orc_h *orc_create(const orc_desc *d, char *err, int errlen)
         for (long idx = 0; idx < v->N; idx++) {
             long p[3];
             coords_of(v, idx, p);
+            /* classes from the refined cells around the node (Sec. 3.2; App. B for
+             * staircase corners): a node whose cells the next level refines is a hole,
+             * one with some refined cells is co-located with a TF node of the child; a
+             * node of a refined level touching a cell its level does not refine lies on
+             * the interface (TF if co-located with a parent node, else hanging), one
+             * touching no refined cell is not a node of the level */
             unsigned char c = ORC_BULK;
             if (l + 1 < h->nl) {
-                int inside_closed = 1, strictly = 1;
-                for (int a = 0; a < D; a++) {
-                    if (h->lev[l + 1].periodic[a]) continue;
-                    long clo = d->box_lo[l + 1][a] << l, chi = d->box_hi[l + 1][a] << l;
-                    if (p[a] < clo || p[a] > chi) inside_closed = 0;
-                    if (p[a] <= clo || p[a] >= chi) strictly = 0;
-                }
-                if (inside_closed) c = strictly ? ORC_HOLE : ORC_TFC;
+                int tot, cnt = refined_cells_around(h, l + 1, p, &tot);
+                if (cnt == tot) c = ORC_HOLE;
+                else if (cnt > 0) c = ORC_TFC;
             }
-            if (l > 0 && c == ORC_BULK) {
-                int on_bnd = 0, all_even = 1;
-                long q[3] = {p[0] - v->off[0], p[1] - v->off[1], p[2] - v->off[2]};
-                for (int a = 0; a < D; a++) {
-                    if (!v->periodic[a] && (q[a] == 0 || q[a] == v->n[a] - 1)) on_bnd = 1;
+            if (l > 0) {
+                int tot, cnt = refined_parent_cells_of_fine(h, l, p, &tot);
+                int all_even = 1;
+                for (int a = 0; a < D; a++)
                     if (mod_l(p[a], 2) != 0) all_even = 0;
-                }
-                if (on_bnd) c = all_even ? ORC_TFP : ORC_IE;
+                if (cnt == 0) c = ORC_HOLE;
+                else if (cnt < tot && c == ORC_BULK) c = all_even ? ORC_TFP : ORC_IE;
+                else if (cnt < tot) FAIL("a level's interface meets its child's region");
             }
             v->cls[idx] = c;
         }
@@ -973,82 +1068,135 @@ static void tf_gradients(orc_h *h, int l, int phase)
     if (bad) set_err(h, "TF gradient stencil leaves the parent's bulk");
 }
 
-/* steps 2g / 3e: 4-point 1-D Lagrange along the interface (tensor order over
- * odd axes, one-sided next to a corner, reading R10) for the missing
- * populations, S and psi (through C) of hanging nodes. */
-static void ie_complete(orc_h *h, int l)
+/* Stencil of the hanging node idx of level l (Sec. 3.2, 4-point 1-D Lagrange along the
+ * interface; reading R10 for boxes and 3-D faces, R15 for 2-D staircases): the level-l
+ * coordinates of its nodes in pts and their weights in w; returns their number (the
+ * tensor product over the node's odd axes), -1 if a node of it is not a TF node. */
+static int ie_stencil(const orc_h *h, int l, long idx, long (*pts)[3], double *w)
 {
-    level_t *v = &h->lev[l];
-    int Q = h->L.Q, D = h->L.D;
+    const level_t *v = &h->lev[l];
+    int D = h->L.D;
     double wc[4], wo[4];
     orc_lagrange4_weights(0, wc);
     orc_lagrange4_weights(1, wo);
+    long p[3], q[3];
+    coords_of(v, idx, p);
+    for (int a = 0; a < 3; a++) q[a] = p[a] - v->off[a];
+    long pos[3][4];
+    double wts[3][4];
+    int cnt[3];
+    for (int a = 0; a < 3; a++) {
+        if (a >= D || mod_l(p[a], 2) == 0) {
+            cnt[a] = 1;
+            pos[a][0] = p[a];
+            wts[a][0] = 1.0;
+            continue;
+        }
+        cnt[a] = 4;
+        long s = q[a];
+        if (D == 2) {
+            /* 2-D (boxes and staircases, reading R15): along the hanging node's odd
+             * axis, the first of the centred and the two one-sided 4-point sets whose
+             * nodes are all TF nodes of the level; where the interface turns within
+             * a coarse cell of the node and none is complete, the linear 2-point
+             * set of the two TF nodes that end the node's edge */
+            static const long cand[3][4] = {{-3, -1, 1, 3}, {-1, 1, 3, 5}, {1, -1, -3, -5}};
+            int pick = -1;
+            for (int k = 0; k < 3 && pick < 0; k++) {
+                int all_tf = 1;
+                for (int m = 0; m < 4; m++) {
+                    long y[3] = {p[0], p[1], p[2]};
+                    y[a] += cand[k][m];
+                    long j = node_at(h, l, y);
+                    if (j < 0 || v->cls[j] != ORC_TFP) all_tf = 0;
+                }
+                if (all_tf) pick = k;
+            }
+            if (pick < 0) {
+                cnt[a] = 2;
+                pos[a][0] = p[a] - 1;
+                pos[a][1] = p[a] + 1;
+                wts[a][0] = wts[a][1] = 0.5;
+            } else {
+                for (int m = 0; m < 4; m++) {
+                    pos[a][m] = p[a] + cand[pick][m];
+                    wts[a][m] = pick == 0 ? wc[m] : wo[m];
+                }
+            }
+            continue;
+        }
+        if (v->periodic[a] || (s - 3 >= 0 && s + 3 <= v->n[a] - 1)) {
+            long o[4] = {-3, -1, 1, 3};
+            for (int k = 0; k < 4; k++) {
+                pos[a][k] = p[a] + o[k];
+                wts[a][k] = wc[k];
+            }
+        } else if (s - 3 < 0) {
+            long o[4] = {-1, 1, 3, 5};
+            for (int k = 0; k < 4; k++) {
+                pos[a][k] = p[a] + o[k];
+                wts[a][k] = wo[k];
+            }
+        } else {
+            long o[4] = {1, -1, -3, -5};
+            for (int k = 0; k < 4; k++) {
+                pos[a][k] = p[a] + o[k];
+                wts[a][k] = wo[k];
+            }
+        }
+    }
+    int m = 0;
+    for (int i0 = 0; i0 < cnt[0]; i0++)
+        for (int i1 = 0; i1 < cnt[1]; i1++)
+            for (int i2 = 0; i2 < cnt[2]; i2++) {
+                long y[3] = {pos[0][i0], pos[1][i1], pos[2][i2]};
+                long j = node_at(h, l, y);
+                if (j < 0 || v->cls[j] != ORC_TFP) return -1;
+                for (int a = 0; a < 3; a++) pts[m][a] = y[a];
+                w[m] = wts[0][i0] * wts[1][i1] * wts[2][i2];
+                m++;
+            }
+    return m;
+}
+
+int orc_ie_stencil(orc_h *h, int l, long idx, long *pts, double *w)
+{
+    if (l < 1 || l >= h->nl || idx < 0 || idx >= h->lev[l].N || h->lev[l].cls[idx] != ORC_IE) return -1;
+    return ie_stencil(h, l, idx, (long (*)[3])pts, w);
+}
+
+/* steps 2g / 3e: the missing populations (M^f), S and psi (through C) of hanging nodes
+ * from their stencil of TF nodes (ie_stencil). */
+static void ie_complete(orc_h *h, int l)
+{
+    level_t *v = &h->lev[l];
+    int Q = h->L.Q;
     int bad = 0;
     ORC_NODE_LOOP
     for (long idx = 0; idx < v->N; idx++) {
         if (v->cls[idx] != ORC_IE) continue;
-        int ok = 1;
-        long p[3], q[3];
-        coords_of(v, idx, p);
-        for (int a = 0; a < 3; a++) q[a] = p[a] - v->off[a];
-        long pos[3][4];
-        double wts[3][4];
-        int cnt[3];
-        for (int a = 0; a < 3; a++) {
-            if (a >= D || mod_l(p[a], 2) == 0) {
-                cnt[a] = 1;
-                pos[a][0] = p[a];
-                wts[a][0] = 1.0;
-                continue;
-            }
-            cnt[a] = 4;
-            long s = q[a];
-            if (v->periodic[a] || (s - 3 >= 0 && s + 3 <= v->n[a] - 1)) {
-                long o[4] = {-3, -1, 1, 3};
-                for (int k = 0; k < 4; k++) {
-                    pos[a][k] = p[a] + o[k];
-                    wts[a][k] = wc[k];
-                }
-            } else if (s - 3 < 0) {
-                long o[4] = {-1, 1, 3, 5};
-                for (int k = 0; k < 4; k++) {
-                    pos[a][k] = p[a] + o[k];
-                    wts[a][k] = wo[k];
-                }
-            } else {
-                long o[4] = {1, -1, -3, -5};
-                for (int k = 0; k < 4; k++) {
-                    pos[a][k] = p[a] + o[k];
-                    wts[a][k] = wo[k];
-                }
-            }
-        }
-        double acc_f[QMAX], acc_S[6], acc_C[6];
-        memset(acc_f, 0, sizeof(acc_f));
-        memset(acc_S, 0, sizeof(acc_S));
-        memset(acc_C, 0, sizeof(acc_C));
-        for (int i0 = 0; i0 < cnt[0]; i0++)
-            for (int i1 = 0; i1 < cnt[1]; i1++)
-                for (int i2 = 0; i2 < cnt[2]; i2++) {
-                    long y[3] = {pos[0][i0], pos[1][i1], pos[2][i2]};
-                    double wgt = wts[0][i0] * wts[1][i1] * wts[2][i2];
-                    long j = node_at(h, l, y);
-                    if (j < 0 || v->cls[j] != ORC_TFP) {
-                        ok = 0;
-                        continue;
-                    }
-                    for (int i = 0; i < Q; i++) acc_f[i] += wgt * v->g[(size_t)i * v->N + j];
-                    for (int k = 0; k < 6; k++) {
-                        acc_S[k] += wgt * v->S[(size_t)k * v->N + j];
-                        acc_C[k] += wgt * v->C[(size_t)k * v->N + j];
-                    }
-                }
-        if (!ok) {
+        long pts[16][3];
+        double wts[16];
+        int n = ie_stencil(h, l, idx, pts, wts);
+        if (n < 0) {
 #ifdef _OPENMP
 #pragma omp atomic write
 #endif
             bad = 1;
             continue;
+        }
+        double acc_f[QMAX], acc_S[6], acc_C[6];
+        memset(acc_f, 0, sizeof(acc_f));
+        memset(acc_S, 0, sizeof(acc_S));
+        memset(acc_C, 0, sizeof(acc_C));
+        for (int m = 0; m < n; m++) {
+            long j = node_at(h, l, pts[m]);
+            double wgt = wts[m];
+            for (int i = 0; i < Q; i++) acc_f[i] += wgt * v->g[(size_t)i * v->N + j];
+            for (int k = 0; k < 6; k++) {
+                acc_S[k] += wgt * v->S[(size_t)k * v->N + j];
+                acc_C[k] += wgt * v->C[(size_t)k * v->N + j];
+            }
         }
         for (int i = 0; i < Q; i++)
             if (!((v->kf[idx] >> i) & 1u)) v->g[(size_t)i * v->N + idx] = acc_f[i];

@@ -39,6 +39,11 @@ typedef struct {
     double sigma;                        /* H-RR hybridisation, 0.98 in the paper */
     int dc_variant;                      /* 2 = DC2 (Table 1), 1 = DC1 */
     int psi_sign;                        /* +1 / -1 multiplier on psi_i */
+    /* Refined region of level l >= 1 as a staircase of parent cells (Sec. 4.1.2, 4.2.2,
+     * App. B): NULL refines every parent cell of the box; otherwise one byte per
+     * parent (level l-1) cell of the box, x fastest, nonzero = refined.  2-D only, on
+     * the finest level, on a box that spans no axis. */
+    const unsigned char *mask[ORC_MAX_LEVELS];
 } orc_desc;
 
 /* lattice tables: c[Q][3], w[Q]; returns Q or -1 */
@@ -94,6 +99,10 @@ int orc_set_pops(orc_h *h, int l, const double *f);
  * coarse node the unscaled values of the last sync sub-step, at hanging nodes the
  * interpolated ones. */
 int orc_get_gradients(orc_h *h, int l, double *S, double *C);
+/* Test accessor: the stencil of hanging node idx of level l, its nodes' level-l
+ * coordinates pts[n][3] and weights w[n] (n <= 16 returned; -1 if idx is no hanging
+ * node or its stencil misses a TF node). */
+int orc_ie_stencil(orc_h *h, int l, long idx, long *pts, double *w);
 int orc_max_newton_iters(orc_h *h);
 long orc_node_updates(orc_h *h);
 const char *orc_error(orc_h *h);

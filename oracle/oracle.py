@@ -56,6 +56,7 @@ class _Desc(C.Structure):
         ("sigma", C.c_double),
         ("dc_variant", C.c_int),
         ("psi_sign", C.c_int),
+        ("mask", C.c_void_p * MAX_LEVELS),
     ]
 
 
@@ -99,6 +100,7 @@ def lib(threaded: bool = False):
         L.orc_lagrange4_weights.argtypes = [C.c_int, dp]
         L.orc_known_from_occupancy.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_threads.argtypes = [C.c_int]
+        L.orc_ie_stencil.argtypes = [C.c_void_p, C.c_int, C.c_long, C.c_void_p, dp]
         _libs[threaded] = L
     return _libs[threaded]
 
@@ -206,7 +208,9 @@ class Hierarchy:
     """A multi-level DC hierarchy advanced by the oracle (Sec. 3.5).
 
     desc keys: lattice (9|19), coarse_n (nx, ny[, nz]), boxes [((lo),(hi)), ...]
-    for levels 1.. in level-0 cell units, nu0, sigma, dc_variant, psi_sign.
+    for levels 1.. in level-0 cell units, nu0, sigma, dc_variant, psi_sign, and
+    optionally masks: per level None or a uint8 array over the parent cells of the
+    level's box (shape (ny, nx) in 2-D, nonzero = refined; a staircase region).
     threaded=True runs the per-node loops of every step on the OpenMP build (same
     arithmetic per node, identical results).
     """
@@ -228,6 +232,14 @@ class Hierarchy:
         d.sigma = float(desc.get("sigma", 0.98))
         d.dc_variant = int(desc.get("dc_variant", 2))
         d.psi_sign = int(desc.get("psi_sign", -1))
+        # staircase regions: masks[l] over the parent cells of level l's box (x fastest)
+        self._masks = []
+        for l, m in enumerate(desc.get("masks") or []):
+            if m is None or l == 0:
+                continue
+            arr = np.ascontiguousarray(np.asarray(m, dtype=np.uint8))
+            self._masks.append(arr)
+            d.mask[l] = arr.ctypes.data
         err = C.create_string_buffer(256)
         self._h = self._L.orc_create(C.byref(d), err, 256)
         if not self._h:
@@ -300,6 +312,15 @@ class Hierarchy:
         if self._L.orc_get_gradients(self._h, l, _dp(S), _dp(Cm)) != 0:
             raise IndexError(l)
         return S, Cm
+
+    def ie_stencil(self, l, idx):
+        """(points [n, 3] in level-l coordinates, weights [n]) of hanging node idx."""
+        pts = np.zeros((16, 3), dtype=np.int64)
+        w = np.zeros(16)
+        n = self._L.orc_ie_stencil(self._h, int(l), int(idx), pts.ctypes.data_as(C.c_void_p), _dp(w))
+        if n < 0:
+            raise ValueError(f"node {idx} of level {l} has no hanging-node stencil")
+        return pts[:n], w[:n]
 
     def set_pops(self, l, f):
         f = _f64(f)

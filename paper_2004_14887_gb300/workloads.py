@@ -248,6 +248,63 @@ def slab3d(nxy=512, nz=256, slab=(96, 160), box=((128, 128, 112), (384, 384, 144
     return d
 
 
+def circle_mask(box, centre, radius):
+    """Staircase refinement region (paper Sec. 4.1.2): the level-0 cells of the box
+    ((lo_x, lo_y), (hi_x, hi_y)) whose centre lies inside the circle; uint8 array of
+    shape (ny, nx) over the box's cells, x fastest."""
+    (lx, ly), (hx, hy) = box
+    y, x = np.meshgrid(np.arange(ly, hy) + 0.5, np.arange(lx, hx) + 0.5, indexing="ij")
+    return ((x - centre[0]) ** 2 + (y - centre[1]) ** 2 < radius * radius).astype(np.uint8)
+
+
+def inclined_mask(box, point, angle_deg):
+    """Staircase refinement region (paper Sec. 4.2.2): the level-0 cells of the box whose
+    centre lies below the line through `point` inclined by angle_deg to the x axis."""
+    (lx, ly), (hx, hy) = box
+    y, x = np.meshgrid(np.arange(ly, hy) + 0.5, np.arange(lx, hx) + 0.5, indexing="ij")
+    t = math.tan(math.radians(angle_deg))
+    return (y < point[1] + t * (x - point[0])).astype(np.uint8)
+
+
+def pulse_circle(n=64, box=((12, 12), (52, 52)), radius=16.0, steps=60, seed=0, storage="f64", nu0=1e-5, A=1e-3,
+                 Rc_fine=3.0, mach=0.0):
+    """2-D acoustic pulse inside a circular refined region (paper Sec. 4.1.2 analogue):
+    D2Q9, two levels, the refined cells those of the box within `radius` of the
+    domain centre; the pulse starts at the centre (seeded jitter) and radiates across
+    the staircase interface."""
+    d = _base(9, (n, n), [box], nu0, storage)
+    c = (0.5 * n, 0.5 * n)
+    d["masks"] = [None, circle_mask(box, c, radius)]
+    rng = np.random.default_rng(seed)
+    jit = rng.uniform(-1.0, 1.0, 2)
+    d["init"] = {"kind": "pulse", "xc": c[0] + jit[0], "yc": c[1] + jit[1], "zc": 0.0, "Rc": Rc_fine / 2.0, "A": A,
+                 "U": (mach * CS, 0.0, 0.0)}
+    d["steps"] = steps
+    d["name"] = f"pulse_circle_{n}"
+    return d
+
+
+def vortex_inclined(n=64, box=((8, 8), (56, 56)), angle=30.0, steps=60, seed=0, storage="f64", nu0=1e-5, swirl=0.05,
+                    mach=0.1, Rc=4.0):
+    """2-D vortex convected across a 30-degree inclined staircase interface (paper Sec.
+    4.2.2 analogue): D2Q9, two levels, the refined cells those of the box below the
+    line through the domain centre at `angle`; the vortex starts below the line and
+    the mean flow carries it across, normal to the line."""
+    d = _base(9, (n, n), [box], nu0, storage)
+    c = (0.5 * n, 0.5 * n)
+    d["masks"] = [None, inclined_mask(box, c, angle)]
+    a = math.radians(angle)
+    nrm = (-math.sin(a), math.cos(a))  # unit normal pointing to the coarse side
+    rng = np.random.default_rng(seed)
+    jit = rng.uniform(-1.0, 1.0, 2)
+    U = mach * CS
+    d["init"] = {"kind": "vortex", "xc": c[0] - 2.0 * Rc * nrm[0] + jit[0], "yc": c[1] - 2.0 * Rc * nrm[1] + jit[1],
+                 "Rc": Rc, "swirl": swirl, "U": (U * nrm[0], U * nrm[1], 0.0)}
+    d["steps"] = steps
+    d["name"] = f"vortex_inclined_{n}"
+    return d
+
+
 def init_fields(desc: dict, l: int):
     """(rho, u) of every node of level l, rho shape (N,), u shape (D, N)."""
     D = 2 if desc["lattice"] == 9 else 3
