@@ -125,6 +125,24 @@ typedef struct lbm_hierarchy *lbm_h;
 LBM_API int lbm_create_hierarchy(const lbm_hierarchy_desc *desc, void *cuda_stream, lbm_h *out);
 LBM_API const char *lbm_create_error(void);
 
+/* The same with staircase refinement interfaces of arbitrary shape (Sec. 4.1.2
+ * circular interface, Sec. 4.2.2 inclined interface, App. B convex and concave
+ * corners): masks[l] (l >= 1; masks and masks[l] may be NULL = the whole box) holds one
+ * byte per cell of level l-1 inside level l's box [box_lo, box_hi) (level-0 cell units
+ * times 2^(l-1) cells per axis, x fastest), nonzero where level l refines the cell; the
+ * caller owns the masks and may free them after the call.  Node classes follow from the
+ * refined cells around each node (a coarse node whose cells are all refined is a hole,
+ * one with some refined cells is co-located with a TF node; a fine node touching an
+ * unrefined cell lies on the interface) and the population sets from reading R4, as for
+ * boxes.  A hanging node interpolates along its odd axis from the first complete set of
+ * TF nodes among the centred (-3, -1, 1, 3) and one-sided (-1, 1, 3, 5) / (1, -1, -3, -5)
+ * 4-point sets, else linearly from the two TF nodes of its edge.  Restrictions, checked
+ * (LBM_ERR_BAD_DESC): D2Q9, masks on the finest level only, on a box that spans no axis,
+ * no two refined cells meeting at a corner only.  Probes are not available on a masked
+ * hierarchy (LBM_ERR_ARG). */
+LBM_API int lbm_create_hierarchy_masked(const lbm_hierarchy_desc *desc, const uint8_t *const *masks,
+                                        void *cuda_stream, lbm_h *out);
+
 /* Box size n[3], box origin (level-l node units) off[3], active node count and tau_l. */
 LBM_API int lbm_query_level(lbm_h h, int level, int64_t n_out[3], int64_t off_out[3], int64_t *n_active,
                     double *tau_out);

@@ -138,6 +138,7 @@ struct LevelDev {
     int fast_lo[3], fast_hi[3];  // tile grown by 2 must stay in [fast_lo, fast_hi]
     int has_child;
     int child_lo[3], child_hi[3], child_per[3];  // closed child box in this level's box coordinates
+    const unsigned char *tile_flags;  // 2-D: per-tile class (staircase regions), else NULL (geometric rule)
     // collision parameters of the level in both arithmetic types (batched launches read them here)
     double om, sigma, spsi;
     float tauf, omf, sigmaf, spsif;

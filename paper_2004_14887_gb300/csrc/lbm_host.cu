@@ -50,6 +50,11 @@ struct Level {
     std::vector<uint8_t> cls;
     std::vector<int> tag;
     std::vector<unsigned char> tile_flag;
+    // per-tile classes of the 2-D bulk kernel for each tile shape, node by node: levels
+    // a staircase region touches (the geometric tile rule assumes boxes)
+    bool use_tflag = false;
+    std::vector<unsigned char> tflag[LBM_TILE_CONFIGS];
+    unsigned char *d_tflag[LBM_TILE_CONFIGS] = {};
     int tiles[3] = {1, 1, 1};
     int nTFP = 0, nIE = 0, nTFC = 0, nif = 0;
     int tile_cfg = 0;  // D2Q9 bulk tile shape (kTileCfgs), chosen by lbm_autotune
@@ -100,6 +105,10 @@ struct lbm_hierarchy {
     int64_t device_bytes = 0;
     int *d_status = nullptr, *d_maxit = nullptr;
     int if_mode = LBM_IFACE_AUTO;  // interface thread mapping (lbm_set_interface_mapping)
+    // staircase regions (lbm_create_hierarchy_masked): per level, the refined parent
+    // cells of its box (x fastest; empty: the whole box)
+    std::vector<uint8_t> mask[LBM_MAX_LEVELS];
+    bool masked = false;
     // test hook of the 3-D bulk kernel's bounded waits (lbm_debug_withhold_copy)
     int withhold_level = -1, withhold_block = -1, withhold_k = -1;
     unsigned long long withhold_limit_ns = 0;
@@ -240,6 +249,65 @@ void global_of(const Level &v, long long idx, int64_t *p)
 }
 
 // ------------------------------------------------------------------ geometry
+// Does level l (>= 1) refine the cell of its parent level l-1 with lower corner c
+// (global level-(l-1) coordinates)?  The box's cells on every axis it does not span,
+// any cell on an axis it spans, and of those the ones its mask marks.
+bool refines(const lbm_h h, int l, const int64_t *c)
+{
+    const lbm_hierarchy_desc &d = h->d;
+    const Level &pv = h->lev[l - 1];
+    int64_t q[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
+    for (int a = 0; a < h->D; a++) {
+        int64_t ca = c[a];
+        if (pv.per[a]) ca = pv.off[a] + emod(ca - pv.off[a], pv.n[a]);
+        if (h->lev[l].per[a]) continue;
+        const int64_t psc = (int64_t)1 << (l - 1), lo = d.box_lo[l][a] * psc, hi = d.box_hi[l][a] * psc;
+        if (ca < lo || ca >= hi) return false;
+        q[a] = ca - lo;
+        ext[a] = hi - lo;
+    }
+    if (h->mask[l].empty()) return true;
+    return h->mask[l][(size_t)(q[0] + ext[0] * (q[1] + ext[1] * q[2]))] != 0;
+}
+
+// refined cells (by level l) among the 2^D cells around node p of level l-1; *tot = 2^D
+int refined_around(const lbm_h h, int l, const int64_t *p, int *tot)
+{
+    int cnt = 0;
+    *tot = 1 << h->D;
+    for (int k = 0; k < *tot; k++) {
+        int64_t c[3] = {p[0], p[1], p[2]};
+        for (int a = 0; a < h->D; a++) c[a] -= (k >> a) & 1;
+        cnt += refines(h, l, c);
+    }
+    return cnt;
+}
+
+// refined cells among the parent cells that node p of level l touches (two per even
+// coordinate, one per odd one); *tot = their number
+int refined_touched(const lbm_h h, int l, const int64_t *p, int *tot)
+{
+    int64_t lo[3] = {0, 0, 0}, cnt_a[3] = {1, 1, 1};
+    for (int a = 0; a < h->D; a++) {
+        if (emod(p[a], 2) == 0) {
+            lo[a] = p[a] / 2 - 1;
+            cnt_a[a] = 2;
+        } else {
+            lo[a] = (p[a] - 1) / 2;
+        }
+    }
+    int cnt = 0;
+    *tot = 0;
+    for (int64_t k2 = 0; k2 < cnt_a[2]; k2++)
+        for (int64_t k1 = 0; k1 < cnt_a[1]; k1++)
+            for (int64_t k0 = 0; k0 < cnt_a[0]; k0++) {
+                const int64_t c[3] = {lo[0] + k0, lo[1] + k1, lo[2] + k2};
+                cnt += refines(h, l, c);
+                (*tot)++;
+            }
+    return cnt;
+}
+
 int build_geometry(lbm_h h)
 {
     const lbm_hierarchy_desc &d = h->d;
@@ -303,7 +371,31 @@ int build_geometry(lbm_h h)
             }
         }
     }
-    // classes
+    // staircase regions: 2-D, the finest level only, a box that spans no axis, and no
+    // two refined cells that meet at a corner only
+    for (int l = 1; l < h->nl; l++) {
+        if (h->mask[l].empty()) continue;
+        if (h->D != 2) return fail(nullptr, LBM_ERR_BAD_DESC, "refinement masks are 2-D only");
+        if (l + 1 < h->nl) return fail(nullptr, LBM_ERR_BAD_DESC, "a refinement mask is allowed on the finest level only");
+        for (int a = 0; a < h->D; a++)
+            if (h->lev[l].per[a]) return fail(nullptr, LBM_ERR_BAD_DESC, "a masked level spans no axis");
+        const int64_t psc = (int64_t)1 << (l - 1);
+        for (int64_t cy = d.box_lo[l][1] * psc; cy <= d.box_hi[l][1] * psc; cy++)
+            for (int64_t cx = d.box_lo[l][0] * psc; cx <= d.box_hi[l][0] * psc; cx++) {
+                const int64_t c00[3] = {cx - 1, cy - 1, 0}, c10[3] = {cx, cy - 1, 0}, c01[3] = {cx - 1, cy, 0},
+                              c11[3] = {cx, cy, 0};
+                const bool a00 = refines(h, l, c00), a10 = refines(h, l, c10), a01 = refines(h, l, c01),
+                           a11 = refines(h, l, c11);
+                if (a00 == a11 && a10 == a01 && a00 != a10)
+                    return fail(nullptr, LBM_ERR_BAD_DESC, "two refined cells meet at a corner only");
+            }
+    }
+    // classes (Sec. 3.2; App. B at staircase corners) from the refined cells around a
+    // node: a node whose cells the next level all refines is a hole, one with some
+    // refined cells is co-located with a TF node of the child; a node of a refined level
+    // that touches a cell its level does not refine lies on the interface (TF when
+    // co-located with a parent node, else hanging); one touching no refined cell is not
+    // a node of the level (a hole of the box)
     for (int l = 0; l < h->nl; l++) {
         Level &v = h->lev[l];
         v.cls.assign(v.N, LBM_NODE_BULK);
@@ -311,23 +403,21 @@ int build_geometry(lbm_h h)
             int64_t p[3];
             global_of(v, idx, p);
             uint8_t c = LBM_NODE_BULK;
-            if (v.has_child) {
-                bool closed = true, strict = true;
-                for (int a = 0; a < h->D; a++) {
-                    if (v.child_per[a]) continue;
-                    if (p[a] < v.child_lo[a] || p[a] > v.child_hi[a]) closed = false;
-                    if (p[a] <= v.child_lo[a] || p[a] >= v.child_hi[a]) strict = false;
-                }
-                if (closed) c = strict ? LBM_NODE_HOLE : LBM_NODE_TF_CHILD;
+            if (l + 1 < h->nl) {
+                int tot = 0;
+                const int cnt = refined_around(h, l + 1, p, &tot);
+                if (cnt == tot) c = LBM_NODE_HOLE;
+                else if (cnt > 0) c = LBM_NODE_TF_CHILD;
             }
-            if (l > 0 && c == LBM_NODE_BULK) {
-                bool outline = false, even = true;
-                for (int a = 0; a < h->D; a++) {
-                    const int64_t q = p[a] - v.off[a];
-                    if (!v.per[a] && (q == 0 || q == v.n[a] - 1)) outline = true;
+            if (l > 0) {
+                int tot = 0;
+                const int cnt = refined_touched(h, l, p, &tot);
+                bool even = true;
+                for (int a = 0; a < h->D; a++)
                     if (emod(p[a], 2) != 0) even = false;
-                }
-                if (outline) c = even ? LBM_NODE_TF_PARENT : LBM_NODE_HANGING;
+                if (cnt == 0) c = LBM_NODE_HOLE;
+                else if (cnt < tot && c == LBM_NODE_BULK) c = even ? LBM_NODE_TF_PARENT : LBM_NODE_HANGING;
+                else if (cnt < tot) return fail(nullptr, LBM_ERR_BAD_DESC, "level %d's interface meets its child's region", l);
             }
             v.cls[idx] = c;
         }
@@ -458,6 +548,35 @@ int build_interfaces(lbm_h h)
                 static const int oc[4] = {-3, -1, 1, 3}, olo[4] = {-1, 1, 3, 5}, ohi[4] = {1, -1, -3, -5};
                 const int *o = oc;
                 const double *w = wc;
+                if (D == 2) {
+                    // 2-D, boxes and staircases (reading R15): the first of the centred and
+                    // the two one-sided 4-point sets along the odd axis made of TF nodes only;
+                    // else the 2-point linear set of the TF nodes that end the node's edge
+                    const int *cand[3] = {oc, olo, ohi};
+                    int pick = -1;
+                    for (int k = 0; k < 3 && pick < 0; k++) {
+                        bool all_tf = true;
+                        for (int m = 0; m < 4 && all_tf; m++) {
+                            int64_t y[3] = {p[0], p[1], p[2]};
+                            y[a] += cand[k][m];
+                            const long long j = node_of(h, l, y);
+                            all_tf = j >= 0 && F.cls[j] == LBM_NODE_TF_PARENT;
+                        }
+                        if (all_tf) pick = k;
+                    }
+                    if (pick < 0) {
+                        cnt[a] = 2;
+                        pos[a][0] = p[a] - 1;
+                        pos[a][1] = p[a] + 1;
+                        wt[a][0] = wt[a][1] = 0.5;
+                    } else {
+                        for (int k = 0; k < 4; k++) {
+                            pos[a][k] = p[a] + cand[pick][k];
+                            wt[a][k] = pick == 0 ? wc[k] : wo[k];
+                        }
+                    }
+                    continue;
+                }
                 if (!F.per[a] && q - 3 < 0) {
                     o = olo;
                     w = wo;
@@ -663,6 +782,7 @@ int check_tiles(lbm_h h)
         for (int l = 0; l < h->nl; l++) {
             const Level &v = h->lev[l];
             const int tx = (int)((v.n[0] + TX - 1) / TX), ty = (int)((v.n[1] + TY - 1) / TY);
+            if (v.use_tflag) h->lev[l].tflag[c].assign((size_t)tx * ty, TILE_GENERAL);
             for (int by = 0; by < ty; by++)
                 for (int bx = 0; bx < tx; bx++) {
                     const int x0 = bx * TX, y0 = by * TY;
@@ -676,6 +796,10 @@ int check_tiles(lbm_h h)
                         for (int64_t x = x0 - 2; fast && x < x0 + TX + 2; x++)
                             fast = v.cls[x + v.n[0] * y] == LBM_NODE_BULK;
                     const unsigned char want = !any ? TILE_SKIP : (fast ? TILE_FAST : TILE_GENERAL);
+                    if (v.use_tflag) {
+                        h->lev[l].tflag[c][(size_t)bx + (size_t)tx * by] = want;
+                        continue;
+                    }
                     if (geometric_class(h, l, t0, T) != want)
                         return fail(nullptr, LBM_ERR_BAD_DESC, "internal: tile (%d,%d) of level %d, shape %d, "
                                     "classified inconsistently", bx, by, l, c);
@@ -691,6 +815,29 @@ std::vector<double> node_weights(const lbm_h h, int l)
     const Level &v = h->lev[l];
     std::vector<double> w(v.N, 0.0);
     const double base = std::ldexp(1.0, -h->D * l);
+    if (v.use_tflag) {
+        // staircase regions: the node's dual cell in 2^D quarters, one per level-l cell
+        // around it; a quarter counts when its cell lies in the level's region and not in
+        // the child's
+        const double q = std::ldexp(1.0, -h->D);
+        for (long long idx = 0; idx < v.N; idx++) {
+            if (v.cls[idx] == LBM_NODE_HOLE) continue;
+            int64_t p[3];
+            global_of(v, idx, p);
+            double acc = 0.0;
+            for (int k = 0; k < (1 << h->D); k++) {
+                int64_t c[3] = {p[0], p[1], p[2]};
+                for (int a = 0; a < h->D; a++) c[a] -= (k >> a) & 1;
+                int64_t cp[3] = {0, 0, 0};  // parent cell holding level-l cell c
+                for (int a = 0; a < h->D; a++) cp[a] = c[a] >= 0 ? c[a] / 2 : -((1 - c[a]) / 2);
+                const bool own = l == 0 || refines(h, l, cp);
+                const bool child = l + 1 < h->nl && refines(h, l + 1, c);
+                if (own && !child) acc += q;
+            }
+            w[idx] = base * acc;
+        }
+        return w;
+    }
     for (long long idx = 0; idx < v.N; idx++) {
         if (v.cls[idx] == LBM_NODE_HOLE) continue;
         int64_t p[3];
@@ -818,6 +965,8 @@ int upload_all(lbm_h h)
         v.if_S = dev_alloc(h, ni * 6 * as);
         v.if_C = dev_alloc(h, ni * 6 * as);
         v.d_wnode = upload(h, node_weights(h, l), &ok);
+        if (v.use_tflag)
+            for (int c = 0; c < LBM_TILE_CONFIGS; c++) v.d_tflag[c] = upload(h, v.tflag[c], &ok);
         if (!ok || !v.if_pop || !v.if_mac || !v.if_S || !v.if_C) return fail(h, LBM_ERR_OOM, "tables of level %d", l);
         CK(cudaMemset(v.if_pop, 0, ni * Q * as));
         CK(cudaMemset(v.if_mac, 0, ni * 4 * as));
@@ -929,6 +1078,7 @@ LevelDev level_dev(const lbm_h h, int l)
     d.spsif = (float)d.spsi;
     tile_bounds(h, l, d.fast_lo, d.fast_hi, d.child_lo, d.child_hi, d.child_per);
     d.has_child = v.has_child ? 1 : 0;
+    d.tile_flags = (h->D == 2 && v.use_tflag) ? v.d_tflag[v.tile_cfg] : nullptr;
     d.ie_base = v.nTFP;
     d.n_ie = v.nIE;
     if (l > 0) {
@@ -1207,7 +1357,20 @@ extern "C" {
 
 const char *lbm_create_error(void) { return g_create_error.c_str(); }
 
+static int create_impl(const lbm_hierarchy_desc *desc, const uint8_t *const *masks, void *cuda_stream, lbm_h *out);
+
 int lbm_create_hierarchy(const lbm_hierarchy_desc *desc, void *cuda_stream, lbm_h *out)
+{
+    return create_impl(desc, nullptr, cuda_stream, out);
+}
+
+int lbm_create_hierarchy_masked(const lbm_hierarchy_desc *desc, const uint8_t *const *masks, void *cuda_stream,
+                                lbm_h *out)
+{
+    return create_impl(desc, masks, cuda_stream, out);
+}
+
+static int create_impl(const lbm_hierarchy_desc *desc, const uint8_t *const *masks, void *cuda_stream, lbm_h *out)
 {
     if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -1235,6 +1398,21 @@ int lbm_create_hierarchy(const lbm_hierarchy_desc *desc, void *cuda_stream, lbm_
     h->nl = desc->n_levels;
     for (int i = 0; i < h->Q; i++)  // s_i = f_i^eq(1, u_shift): w_i for u_shift = 0
         h->shift[i] = (float)(h->Q == 9 ? feq_one<9>(i, 1.0, desc->u_shift) : feq_one<19>(i, 1.0, desc->u_shift));
+    for (int l = 1; l < h->nl && masks; l++) {
+        if (!masks[l]) continue;
+        size_t cells = 1;
+        const int64_t psc = (int64_t)1 << (l - 1);
+        for (int a = 0; a < D; a++) {
+            const int64_t e = (desc->box_hi[l][a] - desc->box_lo[l][a]) * psc;
+            if (e < 1) {
+                delete h;
+                return fail(nullptr, LBM_ERR_BAD_DESC, "level %d: empty box for its mask", l);
+            }
+            cells *= (size_t)e;
+        }
+        h->mask[l].assign(masks[l], masks[l] + cells);
+        h->masked = true;
+    }
     int rc = build_geometry(h);
     if (rc == LBM_OK) rc = build_interfaces(h);
     if (rc != LBM_OK) {
@@ -1242,6 +1420,8 @@ int lbm_create_hierarchy(const lbm_hierarchy_desc *desc, void *cuda_stream, lbm_
         return rc;
     }
     build_tiles(h);
+    for (int l = 1; l < h->nl; l++)
+        if (!h->mask[l].empty()) h->lev[l].use_tflag = h->lev[l - 1].use_tflag = true;
     rc = check_tiles(h);
     if (rc != LBM_OK) {
         delete h;
@@ -1847,6 +2027,7 @@ extern "C" {
 int lbm_set_probes(lbm_h h, int n, const double *xyz, int64_t capacity)
 {
     if (!h || h->batch || !h->members.empty()) return h ? fail(h, LBM_ERR_ARG, "probes belong to single hierarchies") : LBM_ERR_ARG;
+    if (h->masked) return fail(h, LBM_ERR_ARG, "probes take box hierarchies (the finest level holding a point is found by boxes)");
     if (n < 0 || n > 65536 || (n > 0 && !xyz) || capacity < 0 || capacity > (1 << 26))
         return fail(h, LBM_ERR_ARG, "bad probe count, positions or capacity");
     if ((int64_t)n * capacity > ((int64_t)1 << 28)) return fail(h, LBM_ERR_ARG, "probe buffer above 2^28 samples");
@@ -1947,13 +2128,15 @@ static size_t state_bytes(const lbm_h h)
     return b;
 }
 
-// 64-bit FNV-1a of the FP16 storage shift, so that a state is loaded only where its
-// stored populations mean the same values
+// 64-bit FNV-1a of the FP16 storage shift and of the refinement masks, so that a state
+// is loaded only where its stored populations mean the same values on the same nodes
 static uint64_t shift_key(const lbm_h h)
 {
     uint64_t k = 1469598103934665603ull;
     const unsigned char *b = (const unsigned char *)h->shift;
     for (size_t i = 0; i < sizeof(h->shift); i++) k = (k ^ b[i]) * 1099511628211ull;
+    for (int l = 1; l < h->nl; l++)  // and the staircase regions: a state belongs to its geometry
+        for (uint8_t m : h->mask[l]) k = (k ^ (uint64_t)(m != 0)) * 1099511628211ull;
     return k;
 }
 

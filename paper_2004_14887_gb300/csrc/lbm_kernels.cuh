@@ -1177,7 +1177,8 @@ __device__ __forceinline__ bool bulk2d_tile(const LevelDev &Lv, const S *__restr
     const LevelGeo &g = Lv.g;
     const int X0 = bx * TX, Y0 = by * TY;
     const int t0[3] = {X0, Y0, 0}, T[3] = {TX, TY, 1};
-    const unsigned char flag = tile_class<D>(Lv, t0, T);
+    const unsigned char flag =
+        Lv.tile_flags ? Lv.tile_flags[bx + ((Lv.g.n[0] + TX - 1) / TX) * by] : tile_class<D>(Lv, t0, T);
     if (flag == TILE_SKIP) return false;
     const int tid = threadIdx.x;
     const int tx = tid % TX, tr = tid / TX;

@@ -54,7 +54,7 @@ class lbm_hierarchy_desc(C.Structure):
 
 
 EXPORTS = [
-    "lbm_create_hierarchy", "lbm_create_error", "lbm_query_level", "lbm_node_class", "lbm_init_fields",
+    "lbm_create_hierarchy", "lbm_create_hierarchy_masked", "lbm_create_error", "lbm_query_level", "lbm_node_class", "lbm_init_fields",
     "lbm_advance", "lbm_get_macros", "lbm_get_pops", "lbm_reduce", "lbm_check_status", "lbm_max_newton_iters",
     "lbm_timing_enable", "lbm_timing_read", "lbm_launch_count", "lbm_device_bytes", "lbm_synchronize",
     "lbm_last_error", "lbm_destroy", "lbm_reduce_static", "lbm_create_batch", "lbm_batch_member",
@@ -79,6 +79,7 @@ def lib():
     L = C.CDLL(LIB_PATH)
     vp, i64p, dp = C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)
     L.lbm_create_hierarchy.argtypes = [C.POINTER(lbm_hierarchy_desc), vp, C.POINTER(vp)]
+    L.lbm_create_hierarchy_masked.argtypes = [C.POINTER(lbm_hierarchy_desc), C.POINTER(C.c_void_p), vp, C.POINTER(vp)]
     L.lbm_create_error.restype = C.c_char_p
     L.lbm_query_level.argtypes = [vp, C.c_int, i64p, i64p, i64p, dp]
     L.lbm_node_class.argtypes = [vp, C.c_int, vp]
@@ -195,7 +196,17 @@ class Hierarchy:
             d.alloc, d.free = self._alloc.alloc, self._alloc.free
         self._desc = d
         h = C.c_void_p()
-        rc = L.lbm_create_hierarchy(C.byref(d), C.c_void_p(self._stream_obj.cuda_stream), C.byref(h))
+        masks = desc.get("masks")
+        if masks is not None and any(m is not None for m in masks[1:]):
+            # staircase regions: one byte per parent cell of each level's box, x fastest
+            keep = [None if m is None else np.ascontiguousarray(np.asarray(m, dtype=np.uint8)) for m in masks]
+            arr = (C.c_void_p * MAX_LEVELS)()
+            for l, m in enumerate(keep):
+                if l > 0 and m is not None:
+                    arr[l] = m.ctypes.data
+            rc = L.lbm_create_hierarchy_masked(C.byref(d), arr, C.c_void_p(self._stream_obj.cuda_stream), C.byref(h))
+        else:
+            rc = L.lbm_create_hierarchy(C.byref(d), C.c_void_p(self._stream_obj.cuda_stream), C.byref(h))
         if rc != LBM_OK:
             raise LbmError(rc, L.lbm_create_error().decode())
         self._h = h

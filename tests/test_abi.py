@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_2004_14887_gb300 import build as B
@@ -121,3 +122,54 @@ def test_batch_validation_on_the_host(L):
     arr[2].lattice = 19
     assert L.lbm_create_batch(arr, 3, None, C.byref(h)) == lbm.LBM_ERR_BAD_DESC
     assert L.lbm_create_batch(arr, 0, None, C.byref(h)) == lbm.LBM_ERR_ARG
+
+
+def _create_masked(L, desc, masks):
+    d = lbm.make_desc(desc)
+    keep = [None if m is None else np.ascontiguousarray(np.asarray(m, np.uint8)) for m in masks]
+    arr = (C.c_void_p * lbm.MAX_LEVELS)()
+    for l, m in enumerate(keep):
+        if l > 0 and m is not None:
+            arr[l] = m.ctypes.data
+    h = C.c_void_p()
+    rc = L.lbm_create_hierarchy_masked(C.byref(d), arr, None, C.byref(h))
+    if rc == lbm.LBM_OK:
+        L.lbm_destroy(h)
+    return rc
+
+
+def test_staircase_hierarchies_pass_the_host_set_up(L):
+    """Circular and inclined staircase regions and an L-shaped one: classes, interface
+    tables and per-tile classes are built on the host (no GPU: the call stops at the
+    first CUDA call)."""
+    from paper_2004_14887_gb300 import workloads as W
+
+    for d in (W.pulse_circle(), W.vortex_inclined()):
+        rc = _create_masked(L, d, d["masks"])
+        assert rc in (lbm.LBM_OK, lbm.LBM_ERR_CUDA), L.lbm_create_error().decode()
+
+
+@pytest.mark.parametrize("case,match", [
+    ("diagonal", "corner only"),
+    ("not_finest", "finest level"),
+    ("d3q19", "2-D only"),
+    ("spanning", "spans no axis"),
+])
+def test_invalid_staircase_masks_are_rejected(L, case, match):
+    desc = {"lattice": 9, "coarse_n": (32, 32), "boxes": [((8, 8), (24, 24))], "nu0": 1e-5}
+    m = np.ones((16, 16), np.uint8)
+    masks = [None, m]
+    if case == "diagonal":
+        m[8:, 8:] = 0
+        m[:8, :8] = 0  # the two refined quadrants meet at (16, 16) only
+    elif case == "not_finest":
+        desc["boxes"] = [((8, 8), (24, 24)), ((12, 12), (20, 20))]
+        masks = [None, m, None]
+    elif case == "d3q19":
+        desc = {"lattice": 19, "coarse_n": (16, 16, 16), "boxes": [((4, 4, 4), (12, 12, 12))], "nu0": 1e-5}
+        masks = [None, np.ones((8, 8, 8), np.uint8)]
+    elif case == "spanning":
+        desc["boxes"] = [((8, 0), (24, 32))]
+        masks = [None, np.ones((32, 16), np.uint8)]
+    assert _create_masked(L, desc, masks) == lbm.LBM_ERR_BAD_DESC
+    assert re.search(match, L.lbm_create_error().decode())
