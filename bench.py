@@ -339,6 +339,12 @@ def measure_batch(storage, K, Wm, flush, *, sampler_dev=None, ws=1):
         for l in range(m.n_levels):
             r, u = _fields(d, l)
             m.init_fields(l, r, u)
+    # launch structure chosen by the autotuner (it advances the state: initialise again)
+    tuned = b.autotune(reps=3)
+    for d, m in zip(descs, b.members):
+        for l in range(m.n_levels):
+            r, u = _fields(d, l)
+            m.init_fields(l, r, u)
     print(f"[bench] batch2d {storage}: {len(descs)} hierarchies, set-up {time.perf_counter() - tc:.2f} s, "
           f"{b.device_bytes() / 1e9:.2f} GB on the device", file=sys.stderr, flush=True)
     upd = sum(W.updates_per_coarse_step(d) for d in descs)
@@ -375,10 +381,12 @@ def measure_batch(storage, K, Wm, flush, *, sampler_dev=None, ws=1):
     out = {
         "value": ws * feq * K / t / 1e6, "actual_mlups": ws * upd * K / t / 1e6, "ms_per_step": 1e3 * t / K,
         "steps": K, "warmup": Wm, "storage": storage, "hierarchies": len(descs), "gpu_launches": b.launch_count() - n0,
+        "launch_structure": {"chosen": "phases" if tuned["path"] == lbm.BATCH_PHASES else "persistent",
+                             "us_per_step_persistent": tuned["us"][0], "us_per_step_phases": tuned["us"][1]},
         "clocks": clocks, "node_updates_per_step": upd, "fine_equivalent_updates_per_step": feq,
         "roofline": {"bound": "hbm", "achieved": bytes_step / (t / K) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": bytes_step / (t / K) / 1e9 / peak, "traffic": None,
-                     "kernel": "k_batch (the whole step is one persistent launch)",
+                     "kernel": "whole coarse step (k_batch, or k_batch_bulk / k_batch_rh / k_batch_gi per phase)",
                      "algorithmic_bytes_per_launch": bytes_step, "avg_launch_ms": 1e3 * t / K,
                      "peak_source": f"{peak_src} hbm_gbs (of {peak_src})"},
     }

@@ -42,6 +42,8 @@ extern "C" {
 #define LBM_IFACE_AUTO 0
 #define LBM_IFACE_NODE 1
 #define LBM_IFACE_SEGMENT 2
+#define LBM_BATCH_PERSISTENT 0
+#define LBM_BATCH_PHASES 1
 
 #if defined(__GNUC__)
 #define LBM_API __attribute__((visibility("default")))
@@ -248,6 +250,18 @@ LBM_API int lbm_load_state(lbm_h h, const void *buf, size_t len);
  * batch destroys its members. */
 LBM_API int lbm_create_batch(const lbm_hierarchy_desc *descs, int n, void *cuda_stream, lbm_h *out);
 LBM_API int lbm_batch_member(lbm_h batch, int i, lbm_h *member);
+/* Launch structure of lbm_advance on a batch (the same phases of Sec. 3.5 in the same
+ * order, bitwise the same results): LBM_BATCH_PERSISTENT (the default) runs a coarse
+ * step as the one cooperative launch described above; LBM_BATCH_PHASES runs every phase
+ * as one ordinary launch with one block per work item of all members (bulk tiles,
+ * Newton + history, gradients + hanging nodes), ordered by the stream instead of grid
+ * barriers.  lbm_autotune on a batch times both over reps coarse steps of the live
+ * state and keeps the faster; it advances the batch by 2 (reps + 1) coarse steps, so
+ * initialise the members after it; us_out (optional, 2 entries) receives microseconds
+ * per coarse step (persistent, phases).  lbm_batch_get_path returns the structure or
+ * LBM_ERR_ARG. */
+LBM_API int lbm_batch_set_path(lbm_h batch, int path);
+LBM_API int lbm_batch_get_path(lbm_h batch);
 /* Runs the batch's grid barrier alone over one block per SM; block skip_block (if >= 0)
  * leaves without arriving, so the other blocks' waits run out after limit_us
  * microseconds: returns LBM_ERR_TIMEOUT then, LBM_OK when skip_block < 0.  The
@@ -271,7 +285,8 @@ LBM_API int lbm_max_newton_iters(lbm_h h);
  * launch (cfg 0..4).  Synchronises.  lbm_set_tile_config / lbm_get_tile_config set or
  * read a level's configuration directly (e.g. from a cache of earlier autotune
  * results); changing one drops the captured graphs.  Every configuration computes the
- * same per-node arithmetic: results are bitwise identical. */
+ * same per-node arithmetic: results are bitwise identical.  On a batch, lbm_autotune
+ * chooses the batch's launch structure instead (see lbm_batch_set_path). */
 LBM_API int lbm_autotune(lbm_h h, int reps, double *us_out);
 LBM_API int lbm_set_tile_config(lbm_h h, int level, int cfg);
 LBM_API int lbm_get_tile_config(lbm_h h, int level, int *cfg);

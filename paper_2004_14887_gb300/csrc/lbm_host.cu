@@ -136,6 +136,9 @@ struct lbm_hierarchy {
     lbm_hierarchy *batch = nullptr;  // set on members
     BatchDev bdev{};
     BatchPhase *d_phases = nullptr;
+    std::vector<BatchPhase> phases;                    // the same on the host
+    std::vector<int> work_bulk, work_rh, work_gi;      // per level: work items of a phase (all members)
+    int batch_path = LBM_BATCH_PERSISTENT;             // launch structure of lbm_advance on a batch
     int nphases = 0;
     int batch_grid = 0;
 };
@@ -1873,6 +1876,15 @@ int build_batch(lbm_h b)
     emit_phases(ph, 0, 0, L);
     b->d_phases = upload(b, ph, &ok);
     b->nphases = (int)ph.size();
+    b->phases = ph;
+    b->work_bulk.assign(L, 0);
+    b->work_rh.assign(L, 0);
+    b->work_gi.assign(L, 0);
+    for (int l = 0; l < L; l++) {
+        b->work_bulk[l] = pre_bulk[(size_t)l * (n + 1) + n];
+        b->work_rh[l] = pre_rh[(size_t)l * (n + 1) + n];
+        b->work_gi[l] = pre_gi[(size_t)l * (n + 1) + n];
+    }
     unsigned int *bar = (unsigned int *)dev_alloc(b, 4 * sizeof(unsigned int));
     b->d_status = (int *)dev_alloc(b, 2 * sizeof(int));
     if (!ok || !bar || !b->d_status) return fail(b, LBM_ERR_OOM, "batch tables");
@@ -1911,6 +1923,38 @@ int batch_launch(lbm_h b, long long k0, int nsteps)
 }
 }  // namespace
 
+// The phase-launch structure: one launch per phase of the sub-cycle schedule, one CTA
+// per work item of all members (k_batch_bulk / k_batch_rh / k_batch_gi).
+template <typename S>
+int batch_launch_phases(lbm_h b, long long k0, int nsteps)
+{
+    lbm_h h = b;
+    const BatchDev B = b->bdev;
+    for (int st = 0; st < nsteps; st++) {
+        const long long k = k0 + st;
+        for (const BatchPhase &ph : b->phases) {
+            const int l = ph.level;
+            const long long kl = (k << l) + ph.sub;
+            if (ph.kind == PH_BULK) {
+                if (b->work_bulk[l] > 0)
+                    launch_chained(k_batch_bulk<9, S, T2X, T2YT, T2NR>, dim3(b->work_bulk[l]), dim3(kBatchThreads), 0,
+                                   b->stream, B, l, kl);
+            } else if (ph.kind == PH_RH) {
+                const TimeW tw = l > 0 ? time_weights((int)(kl & 1), kl >> 1) : TimeW{};
+                if (b->work_rh[l] > 0)
+                    launch_chained(k_batch_rh<9, S>, dim3(b->work_rh[l]), dim3(kBatchThreads), 0, b->stream, B, l, kl, tw);
+            } else {
+                const TimeW tw = time_weights((int)(kl & 1), kl >> 1);
+                if (b->work_gi[l] > 0)
+                    launch_chained(k_batch_gi<9, S>, dim3(b->work_gi[l]), dim3(kBatchThreads), 0, b->stream, B, l, kl, tw);
+            }
+            b->launches++;
+        }
+    }
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
 static int batch_advance(lbm_h b, int64_t n)
 {
     lbm_h h = b;
@@ -1921,11 +1965,17 @@ static int batch_advance(lbm_h b, int64_t n)
     for (int64_t done = 0; done < n;) {
         const int chunk = (int)std::min<int64_t>(n - done, 1 << 20);
         int rc;
-        if (b->d.storage == LBM_F64) rc = batch_launch<double>(b, k + done, chunk);
-        else if (b->d.storage == LBM_F32) rc = batch_launch<float>(b, k + done, chunk);
-        else rc = batch_launch<__half>(b, k + done, chunk);
+        if (b->batch_path == LBM_BATCH_PHASES) {
+            if (b->d.storage == LBM_F64) rc = batch_launch_phases<double>(b, k + done, chunk);
+            else if (b->d.storage == LBM_F32) rc = batch_launch_phases<float>(b, k + done, chunk);
+            else rc = batch_launch_phases<__half>(b, k + done, chunk);
+        } else {
+            if (b->d.storage == LBM_F64) rc = batch_launch<double>(b, k + done, chunk);
+            else if (b->d.storage == LBM_F32) rc = batch_launch<float>(b, k + done, chunk);
+            else rc = batch_launch<__half>(b, k + done, chunk);
+            b->launches++;
+        }
         if (rc != LBM_OK) return rc;
-        b->launches++;
         done += chunk;
     }
     for (auto *m : b->members) m->ncoarse += n;
@@ -2280,10 +2330,56 @@ int lbm_get_tile_config(lbm_h h, int level, int *cfg)
     return LBM_OK;
 }
 
+int lbm_batch_set_path(lbm_h b, int path)
+{
+    if (!b || b->members.empty()) return b ? fail(b, LBM_ERR_ARG, "not a batch") : LBM_ERR_ARG;
+    if (path != LBM_BATCH_PERSISTENT && path != LBM_BATCH_PHASES) return fail(b, LBM_ERR_ARG, "unknown launch structure %d", path);
+    b->batch_path = path;
+    return LBM_OK;
+}
+
+int lbm_batch_get_path(lbm_h b)
+{
+    if (!b || b->members.empty()) return b ? fail(b, LBM_ERR_ARG, "not a batch") : LBM_ERR_ARG;
+    return b->batch_path;
+}
+
+// batches: the launch structure of a coarse step (one persistent launch, or one launch
+// per phase), each timed over reps coarse steps of the live state, the faster kept
+static int autotune_batch(lbm_h b, int reps, double *us_out)
+{
+    lbm_h h = b;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double us[2] = {0.0, 0.0};
+    const int paths[2] = {LBM_BATCH_PERSISTENT, LBM_BATCH_PHASES};
+    for (int p = 0; p < 2; p++) {
+        b->batch_path = paths[p];
+        int rc = batch_advance(b, 1);  // warm-up
+        if (rc != LBM_OK) return rc;
+        CK(cudaEventRecord(e0, b->stream));
+        rc = batch_advance(b, reps);
+        if (rc != LBM_OK) return rc;
+        CK(cudaEventRecord(e1, b->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        us[p] = 1e3 * ms / reps;
+        if (us_out) us_out[p] = us[p];
+    }
+    b->batch_path = us[1] < us[0] ? LBM_BATCH_PHASES : LBM_BATCH_PERSISTENT;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
 int lbm_autotune(lbm_h h, int reps, double *us_out)
 {
-    if (!h || h->batch || !h->members.empty()) return h ? fail(h, LBM_ERR_ARG, "autotune single hierarchies") : LBM_ERR_ARG;
+    if (!h || h->batch) return h ? fail(h, LBM_ERR_ARG, "autotune a hierarchy or a whole batch") : LBM_ERR_ARG;
     if (reps < 1 || reps > 10000) return fail(h, LBM_ERR_ARG, "reps must be in [1, 10000]");
+    if (!h->members.empty()) return autotune_batch(h, reps, us_out);
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));

@@ -1609,6 +1609,50 @@ __global__ void __launch_bounds__(TX *TYT, sizeof(S) == 8 ? 1 : 3)
     }
 }
 
+// Phase-launch structure of a batch (the alternative to k_batch): every phase of the
+// sub-cycle schedule is one ordinary launch with one CTA per work item of all members,
+// so no CTA stays resident and no grid barrier is needed (kernel boundaries order
+// dependent phases).  The bodies are the ones of k_batch: the results are bitwise the
+// same.
+template <int Q, typename S, int TX, int TYT, int NR>
+__global__ void __launch_bounds__(TX *TYT, sizeof(S) == 8 ? 1 : (TX * TYT >= 256 ? 1024 / (TX * TYT) : 4))
+    k_batch_bulk(BatchDev B, int l, long long kl)
+{
+    pdl_enter();
+    using R = typename St<S>::R;
+    __shared__ LevelDev s_lv;
+    const int *pre = B.pre_bulk + (size_t)l * (B.n + 1);
+    const int t = blockIdx.x;
+    const int h = owner(pre, B.n, t);
+    const int *src = (const int *)&B.lev[h * B.L + l];
+    for (int w = threadIdx.x; w < (int)(sizeof(LevelDev) / 4); w += blockDim.x) ((int *)&s_lv)[w] = src[w];
+    __syncthreads();
+    const bool dbl = sizeof(R) == 8;
+    const int local = t - pre[h];
+    bulk2d_tile<Q, S, TX, TYT, NR, 1>(s_lv, (const S *)s_lv.f[kl & 1], (S *)s_lv.f[(kl + 1) & 1],
+                                      dbl ? (R)s_lv.tau : (R)s_lv.tauf, dbl ? (R)s_lv.om : (R)s_lv.omf,
+                                      dbl ? (R)s_lv.sigma : (R)s_lv.sigmaf, dbl ? (R)s_lv.spsi : (R)s_lv.spsif,
+                                      local % s_lv.tiles[0], local / s_lv.tiles[0]);
+}
+template <int Q, typename S>
+__global__ void __launch_bounds__(256) k_batch_rh(BatchDev B, int l, long long kl, TimeW tw)
+{
+    pdl_enter();
+    const int *pre = B.pre_rh + (size_t)l * (B.n + 1);
+    const int t = blockIdx.x;
+    const int h = owner(pre, B.n, t);
+    batch_recon_hist<Q, S>(B, h, l, kl, t - pre[h], tw);
+}
+template <int Q, typename S>
+__global__ void __launch_bounds__(256) k_batch_gi(BatchDev B, int l, long long kl, TimeW tw)
+{
+    pdl_enter();
+    const int *pre = B.pre_gi + (size_t)l * (B.n + 1);
+    const int t = blockIdx.x;
+    const int h = owner(pre, B.n, t);
+    batch_grad_ie<Q, S>(B, h, l, kl, t - pre[h], tw);
+}
+
 // The barrier alone, for the bounded-wait check: with skip >= 0 that block returns
 // without arriving, so every other block's wait runs out and sets ST_TIMEOUT.
 __global__ void k_barrier_check(unsigned int *count, unsigned int *gen, int *status, unsigned long long limit_ns,

@@ -60,10 +60,11 @@ EXPORTS = [
     "lbm_last_error", "lbm_destroy", "lbm_reduce_static", "lbm_create_batch", "lbm_batch_member",
     "lbm_batch_check_barrier", "lbm_set_probes", "lbm_get_probes", "lbm_save_state", "lbm_load_state",
     "lbm_autotune", "lbm_set_tile_config", "lbm_get_tile_config", "lbm_set_interface_mapping",
-    "lbm_reduce_async", "lbm_debug_withhold_copy",
+    "lbm_reduce_async", "lbm_debug_withhold_copy", "lbm_batch_set_path", "lbm_batch_get_path",
 ]
 TILE_CONFIGS = 5
 IFACE_AUTO, IFACE_NODE, IFACE_SEGMENT = 0, 1, 2
+BATCH_PERSISTENT, BATCH_PHASES = 0, 1
 
 _lib = None
 
@@ -114,6 +115,8 @@ def lib():
     L.lbm_set_tile_config.argtypes = [vp, C.c_int, C.c_int]
     L.lbm_set_interface_mapping.argtypes = [vp, C.c_int]
     L.lbm_get_tile_config.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
+    L.lbm_batch_set_path.argtypes = [vp, C.c_int]
+    L.lbm_batch_get_path.argtypes = [vp]
     L.lbm_debug_withhold_copy.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64]
     _lib = L
     return L
@@ -486,6 +489,21 @@ class Batch:
 
     def check_status(self):
         self._check(lib().lbm_check_status(self._h))
+
+    def set_path(self, path):
+        """BATCH_PERSISTENT (one cooperative launch per coarse step) or BATCH_PHASES (one
+        launch per phase)."""
+        self._check(lib().lbm_batch_set_path(self._h, int(path)))
+
+    def path(self):
+        return lib().lbm_batch_get_path(self._h)
+
+    def autotune(self, reps=5):
+        """Time both launch structures over reps coarse steps of the live state and keep
+        the faster (the state advances: initialise the members afterwards)."""
+        us = (C.c_double * 2)()
+        self._check(lib().lbm_autotune(self._h, int(reps), us))
+        return {"path": self.path(), "us": [us[0], us[1]]}
 
     def check_barrier(self, skip_block, limit_us):
         return lib().lbm_batch_check_barrier(self._h, int(skip_block), int(limit_us))

@@ -82,3 +82,45 @@ def test_batch_barrier_wait_is_bounded():
     b.check_status()
     with pytest.raises(lbm.LbmError):
         b.members[0].advance(1)  # a member advances only with its batch
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s"])
+def test_phase_launches_equal_the_persistent_launch(storage):
+    """The two launch structures of a batch (one cooperative launch per coarse step, or
+    one launch per phase) run the same phase bodies in the same order: bitwise equal
+    members after the same steps, also when the structure changes between calls."""
+    descs = _small_batch(storage)
+    out = []
+    for paths in ([lbm.BATCH_PERSISTENT], [lbm.BATCH_PHASES], [lbm.BATCH_PHASES, lbm.BATCH_PERSISTENT]):
+        b = lbm.Batch(descs)
+        for d, m in zip(descs, b.members):
+            for l in range(m.n_levels):
+                r, u = W.init_fields(d, l)
+                m.init_fields(l, r, u)
+        for p in paths:
+            b.set_path(p)
+            assert b.path() == p
+            b.advance(6)
+        b.check_status()
+        out.append([[m.get_pops(l) for l in range(m.n_levels)] for m in b.members])
+        b.close()
+    steps = {0: 6, 1: 6, 2: 12}
+    assert steps[0] == steps[1]
+    for ma, mb in zip(out[0], out[1]):
+        for a, c in zip(ma, mb):
+            assert np.array_equal(a, c)
+
+
+def test_batch_autotune_chooses_a_launch_structure():
+    descs = _small_batch("f32")
+    b = lbm.Batch(descs)
+    for d, m in zip(descs, b.members):
+        for l in range(m.n_levels):
+            r, u = W.init_fields(d, l)
+            m.init_fields(l, r, u)
+    res = b.autotune(reps=3)
+    assert res["path"] in (lbm.BATCH_PERSISTENT, lbm.BATCH_PHASES)
+    assert all(t > 0 for t in res["us"])
+    assert res["path"] == (lbm.BATCH_PHASES if res["us"][1] < res["us"][0] else lbm.BATCH_PERSISTENT)
+    b.advance(2)
+    b.check_status()
