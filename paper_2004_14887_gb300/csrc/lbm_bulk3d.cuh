@@ -42,6 +42,36 @@ constexpr unsigned cz_mask(int sign)
 }
 constexpr unsigned kCzPlus = cz_mask(1), kCzMinus = cz_mask(-1);
 
+// Runs of consecutive populations (storage order) with the same c_z: the populations of a
+// run stream from the same plane, so one tensor copy of depth 1, 2, 4 or 5 in the
+// population axis moves the whole run.  D3Q19: 0-4, 5, 6, 7-10, 11, 12-13, 14-15, 16-17, 18.
+constexpr int kRuns = 9;
+constexpr int run_start(int j)
+{
+    int r = 0, i = 0;
+    while (r < j) {
+        int e = i + 1;
+        while (e < 19 && Lat<19>::c(e, 2) == Lat<19>::c(i, 2)) e++;
+        i = e;
+        r++;
+    }
+    return i;
+}
+constexpr int run_len(int j)
+{
+    const int i = run_start(j);
+    int e = i + 1;
+    while (e < 19 && Lat<19>::c(e, 2) == Lat<19>::c(i, 2)) e++;
+    return e - i;
+}
+static_assert(run_start(kRuns) == 19, "nine runs cover the 19 populations");
+// tensor map of a run: box depth 1, 2, 4 or 5 populations
+constexpr int depth_map(int len) { return len == 1 ? 0 : (len == 2 ? 1 : (len == 4 ? 2 : 3)); }
+constexpr int kDepths[4] = {1, 2, 4, 5};
+struct alignas(64) TMaps {
+    CUtensorMap m[4];  // boxes of 1, 2, 4 and 5 populations
+};
+
 // shapes of the 3-D staged kernel for storage S and a TX x TY column
 template <int Q, typename S, int TX, int TY>
 struct Stage3 {
@@ -255,7 +285,7 @@ __device__ __forceinline__ void hrr_pairs19(R rho, const R *u, const R *Pq, cons
 // them runs out.
 template <int Q, typename S, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
-    k_bulk3d(const __grid_constant__ CUtensorMap tmap, LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
+    k_bulk3d(const __grid_constant__ TMaps tmaps, LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
              typename St<S>::R tau, typename St<S>::R om, typename St<S>::R sigma, typename St<S>::R spsi, int zc,
              int *status, unsigned long long limit_ns, int withhold_block, int withhold_k)
 {
@@ -341,10 +371,11 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
     const int K = ze - zb + 2;  // planes zb-1 .. ze: macros of all, collisions of zb .. ze-1
     // class of plane k: a plane off a non-periodic box counts as a hole plane (no stage)
     auto plane_of = [&](int k) { return zb - 1 + k; };
+    const PlaneRule rule(Lv, X0, Y0, TX, TY);
     auto class_of = [&](int k) {
         const int p = plane_of(k);
         if (!g.per[2] && (p < 0 || p >= g.n[2])) return (int)LOAD_HOLE;
-        return plane_class(Lv, X0, Y0, TX, TY, p);
+        return rule(p);
     };
     unsigned phase = 0u, pending = 0u;  // per stage: parity of the next wait, copy in flight
     auto issue = [&](int k, int cls_k) {
@@ -353,18 +384,26 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
         const int s = k & 1, p = plane_of(k);
         S *dst = stage(s);
         if (!seam) {
-            // the last warp issues the copies, one population per lane, after its lane 0
-            // has armed the stage's barrier with the byte count of all of them
+            // the last warp issues the copies, one run of populations per lane, after its
+            // lane 0 has armed the stage's barrier with the byte count of all of them
             if (tid >= NT - 32) {
                 const int lane = tid & 31;
                 if (lane == 0) tma::mbar_expect_tx(&bar[s], (unsigned)G::stage_bytes);
                 __syncwarp();
-                if (lane < Q) {
-                    const int cz = ((kCzPlus >> lane) & 1u) ? 1 : (((kCzMinus >> lane) & 1u) ? -1 : 0);
+                if (lane < kRuns) {
+                    int i0 = 0, mi = 0;
+                    static_for<kRuns>([&](auto jc) {
+                        constexpr int j = decltype(jc)::value;
+                        if (lane == j) {
+                            i0 = run_start(j);
+                            mi = depth_map(run_len(j));
+                        }
+                    });
+                    const int cz = ((kCzPlus >> i0) & 1u) ? 1 : (((kCzMinus >> i0) & 1u) ? -1 : 0);
                     int zq = p - cz;
                     if (g.per[2]) zq = zq < 0 ? zq + g.n[2] : (zq >= g.n[2] ? zq - g.n[2] : zq);
                     tma::fence_proxy_async();
-                    tma::load4d(dst + lane * BOX, &tmap, &bar[s], X0 - XA, Y0 - 2, zq, lane);
+                    tma::load4d(dst + i0 * BOX, &tmaps.m[mi], &bar[s], X0 - XA, Y0 - 2, zq, i0);
                 }
             }
             pending |= 1u << s;

@@ -59,7 +59,7 @@ struct Level {
     int nTFP = 0, nIE = 0, nTFC = 0, nif = 0;
     int tile_cfg = 0;  // D2Q9 bulk tile shape (kTileCfgs), chosen by lbm_autotune
     int zc = 1;        // D3Q19: planes per z chunk of the bulk kernel
-    CUtensorMap tmap[2];  // D3Q19: bulk tensor copy maps of f[0], f[1]
+    TMaps tmap[2];  // D3Q19: bulk tensor copy maps of f[0], f[1] (boxes of 1, 2, 4, 5 populations)
     int64_t n_active = 0;
     // child-box in this level's node coordinates, for volume weights
     bool has_child = false;
@@ -912,7 +912,8 @@ int plan_chunks(lbm_h h, int l)
 }
 
 // 4-D maps (x, y, z, population) of both population buffers of a 3-D level; the box is
-// one population over TX + 2 XA x TY + 4 nodes of one plane (Stage3)
+// TX + 2 XA x TY + 4 nodes of one plane (Stage3) and 1, 2, 4 or 5 consecutive
+// populations (one map per depth: a run of populations with the same c_z is one copy)
 int make_tensor_maps(lbm_h h, int l)
 {
     Level &v = h->lev[l];
@@ -926,14 +927,16 @@ int make_tensor_maps(lbm_h h, int l)
                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     const cuuint64_t dims[4] = {(cuuint64_t)v.n[0], (cuuint64_t)v.n[1], (cuuint64_t)v.n[2], (cuuint64_t)h->Q};
     const cuuint64_t strides[3] = {(cuuint64_t)(v.px * es), (cuuint64_t)(v.px * v.n[1] * es), (cuuint64_t)(v.pitch * es)};
-    const cuuint32_t box[4] = {(cuuint32_t)(T3X + 2 * xa), (cuuint32_t)(T3Y + 4), 1, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
-    for (int k = 0; k < 2; k++) {
-        const CUresult r = enc(&v.tmap[k], dt, 4, v.f[k], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return fail(h, LBM_ERR_CUDA, "tensor map of level %d buffer %d (driver error %d)", l, k, (int)r);
-    }
+    for (int k = 0; k < 2; k++)
+        for (int m = 0; m < 4; m++) {
+            const cuuint32_t box[4] = {(cuuint32_t)(T3X + 2 * xa), (cuuint32_t)(T3Y + 4), 1, (cuuint32_t)kDepths[m]};
+            const CUresult r = enc(&v.tmap[k].m[m], dt, 4, v.f[k], dims, strides, box, estr,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS)
+                return fail(h, LBM_ERR_CUDA, "tensor map of level %d buffer %d (driver error %d)", l, k, (int)r);
+        }
     return LBM_OK;
 }
 
