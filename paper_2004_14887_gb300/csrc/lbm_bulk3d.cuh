@@ -17,8 +17,8 @@
 //            eight carried moments (rho, sum f, Pi) in the pair form of Eq.
 //            (LBMscheme_reg): f_i, f_opp(i) = w_i (E +- O), E even and O odd in c_i
 //   in-plane differences of plane p from the ring (128-bit shared loads)
-// Interface nodes take populations and macros from the level's interface table and
-// S, C from its rows (TF) or by the 4-point stencil of their TF row (hanging).
+// Interface nodes take populations, macros, S and C from the level's interface table
+// (the S and C rows of hanging nodes are interpolated from the TF rows beforehand).
 #pragma once
 
 #include "lbm_kernels.cuh"
@@ -285,7 +285,7 @@ __device__ __forceinline__ void hrr_pairs19(R rho, const R *u, const R *Pq, cons
 // them runs out.
 template <int Q, typename S, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
-    k_bulk3d(const __grid_constant__ TMaps tmaps, LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
+    k_bulk3d(const __grid_constant__ TMaps tmaps, const __grid_constant__ LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
              typename St<S>::R tau, typename St<S>::R om, typename St<S>::R sigma, typename St<S>::R spsi, int zc,
              int *status, unsigned long long limit_ns, int withhold_block, int withhold_k)
 {
@@ -339,6 +339,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
     const int own_b = (ty + 2) * BW + (tx + XA);
     const int halo_b = (hy + 1) * BW + (hx - 1 + XA);
     const int n01 = g.px * g.n[1];
+    const long long pitch = g.pitch;
     // a column whose stage would cross a periodic seam in x or y is filled by plain loads
     const bool seam = (g.per[0] && (X0 - 2 < 0 || X0 + TX + 1 > g.n[0] - 1)) ||
                       (g.per[1] && (Y0 - 2 < 0 || Y0 + TY + 1 > g.n[1] - 1));
@@ -636,35 +637,21 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
                 Cv[4] = sc[9] + dz[ZV_PXZZ];
                 Cv[5] = sc[10] + dz[ZV_PYZZ];
             } else {
+                // interface node: S and C from its table row (TF rows by the gradient
+                // launch, hanging-node rows interpolated from them by k_ie_sc)
                 const R *tS = (const R *)Lv.if_S, *tC = (const R *)Lv.if_C;
-                if (tc >= Lv.ie_base && tc < Lv.ie_base + Lv.n_ie) {
-                    // hanging node: S and C by the same 4-point stencil as its missing populations
-                    const int e = tc - Lv.ie_base, nst = Lv.ie_nst[e];
 #pragma unroll
-                    for (int q = 0; q < 6; q++) Sv[q] = Cv[q] = R(0);
-                    for (int j = 0; j < nst; j++) {
-                        const int tf = Lv.ie_st[e * 16 + j];
-                        const R wj = ((const R *)Lv.ie_w)[e * 16 + j];
-#pragma unroll
-                        for (int q = 0; q < 6; q++) {
-                            Sv[q] += wj * tS[(long long)q * Lv.nif + tf];
-                            Cv[q] += wj * tC[(long long)q * Lv.nif + tf];
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 6; q++) {
-                        Sv[q] = tS[(long long)q * Lv.nif + tc];
-                        Cv[q] = tC[(long long)q * Lv.nif + tc];
-                    }
+                for (int q = 0; q < 6; q++) {
+                    Sv[q] = tS[(long long)q * Lv.nif + tc];
+                    Cv[q] = tC[(long long)q * Lv.nif + tc];
                 }
             }
             S *dst = fdst + (x + g.px * y + (long long)n01 * z);
             hrr_pairs19<R, SHIFT>(rho_c, z0, pq_c, Sv, Cv, tau, om, sigma, spsi, Lv.she, Lv.sho,
                                   [&](auto ic, R v) {
                                       constexpr int i = decltype(ic)::value;
-                                      if constexpr (SHIFT) dst[(long long)i * g.pitch] = __float2half_rn(v);
-                                      else dst[(long long)i * g.pitch] = v;
+                                      if constexpr (SHIFT) dst[(long long)i * pitch] = __float2half_rn(v);
+                                      else dst[(long long)i * pitch] = v;
                                   });
         }
         if (!tma::mbar_wait(&bar[2], (unsigned)k & 1u, limit_ns)) s_timeout = 1;  // a warp that never arrives

@@ -97,9 +97,11 @@ struct lbm_hierarchy {
     // level's sub-steps (fork and join events per level; captured as graph branches)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork[LBM_MAX_LEVELS] = {}, ev_join[LBM_MAX_LEVELS] = {};
-    // third stream: a level's bulk launch starts once its child's sync sub-step has
-    // written this level's child-TF rows (ev_parent) and runs beside the child's rest
-    cudaStream_t side2 = nullptr;
+    // one more stream per level with a child: the level's bulk launch starts once its
+    // child's sync sub-step has written this level's child-TF rows (ev_parent) and runs
+    // beside the child's rest; a stream per level lets a coarse level's bulk launch run
+    // beside its grandchild's sub-steps instead of queueing behind its child's bulk launch
+    cudaStream_t side2[LBM_MAX_LEVELS] = {};
     cudaEvent_t ev_parent[LBM_MAX_LEVELS] = {}, ev_bulk[LBM_MAX_LEVELS] = {};
     std::vector<DevBuf> bufs;
     int64_t device_bytes = 0;
@@ -1232,6 +1234,12 @@ struct Sched {
                 launch_chained(per == 128 ? k_grad_ie<Q, S, true> : k_grad_ie<Q, S, false>, dim3(nbg + nbi), dim3(128), 0,
                                st, I, dv, level_dev(h, l - 1), (const S *)fA, tw, phase, nbg);
                 h->launch_counter++;
+                if (Lat<Q>::D == 3 && dv.n_ie > 0) {
+                    // S and C of the hanging nodes from the TF rows just written (the 3-D
+                    // bulk kernel reads them as table rows)
+                    launch_chained(k_ie_sc<typename St<S>::R>, dim3((dv.n_ie + 127) / 128), dim3(128), 0, st, dv);
+                    h->launch_counter++;
+                }
                 if (forked) cudaEventRecord(h->ev_join[l], h->side);
             }
         }
@@ -1245,10 +1253,10 @@ struct Sched {
         if (l + 1 < h->nl && !h->timing) {
             // this level's bulk launch beside the rest of the child's sync sub-step; the
             // main stream joins it before anything can read this level's new state
-            cudaStreamWaitEvent(h->side2, h->ev_parent[l + 1], 0);
-            if (forked) cudaStreamWaitEvent(h->side2, h->ev_join[l], 0);
-            bulk(h, l, fA, fB, h->side2);
-            cudaEventRecord(h->ev_bulk[l], h->side2);
+            cudaStreamWaitEvent(h->side2[l], h->ev_parent[l + 1], 0);
+            if (forked) cudaStreamWaitEvent(h->side2[l], h->ev_join[l], 0);
+            bulk(h, l, fA, fB, h->side2[l]);
+            cudaEventRecord(h->ev_bulk[l], h->side2[l]);
             cudaStreamWaitEvent(h->stream, h->ev_bulk[l], 0);
         } else {
             if (forked) cudaStreamWaitEvent(h->stream, h->ev_join[l], 0);
@@ -1451,10 +1459,10 @@ static int create_impl(const lbm_hierarchy_desc *desc, const uint8_t *const *mas
         }
         h->own_stream = true;
     }
-    bool evok = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) == cudaSuccess &&
-                cudaStreamCreateWithFlags(&h->side2, cudaStreamNonBlocking) == cudaSuccess;
+    bool evok = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) == cudaSuccess;
     for (int l = 0; l < LBM_MAX_LEVELS && evok; l++)
-        evok = cudaEventCreateWithFlags(&h->ev_fork[l], cudaEventDisableTiming) == cudaSuccess &&
+        evok = (l + 1 >= h->nl || cudaStreamCreateWithFlags(&h->side2[l], cudaStreamNonBlocking) == cudaSuccess) &&
+               cudaEventCreateWithFlags(&h->ev_fork[l], cudaEventDisableTiming) == cudaSuccess &&
                cudaEventCreateWithFlags(&h->ev_join[l], cudaEventDisableTiming) == cudaSuccess &&
                cudaEventCreateWithFlags(&h->ev_parent[l], cudaEventDisableTiming) == cudaSuccess &&
                cudaEventCreateWithFlags(&h->ev_bulk[l], cudaEventDisableTiming) == cudaSuccess;
@@ -1717,10 +1725,14 @@ void lbm_destroy(lbm_h h)
         if (h->d.free) h->d.free(b.p, h->d.alloc_ctx);
         else cudaFree(b.p);
     }
-    for (cudaStream_t s2 : {h->side, h->side2})
-        if (s2) {
-            cudaStreamSynchronize(s2);
-            cudaStreamDestroy(s2);
+    if (h->side) {
+        cudaStreamSynchronize(h->side);
+        cudaStreamDestroy(h->side);
+    }
+    for (int l = 0; l < LBM_MAX_LEVELS; l++)
+        if (h->side2[l]) {
+            cudaStreamSynchronize(h->side2[l]);
+            cudaStreamDestroy(h->side2[l]);
         }
     for (int l = 0; l < LBM_MAX_LEVELS; l++)
         for (cudaEvent_t e : {h->ev_fork[l], h->ev_join[l], h->ev_parent[l], h->ev_bulk[l]})

@@ -1000,9 +1000,11 @@ __device__ __forceinline__ void pdl_enter()
 // interface whose inputs were all written by earlier launches).  NODE selects one node
 // per thread (large interfaces) or one W-lane segment per node (small ones).
 template <int Q, typename S, bool NODE>
-__global__ void __launch_bounds__(128) k_recon_hist(IfaceDev Ir, LevelDev F, LevelDev Cl, const S *__restrict__ ff,
-                                                      TimeW tw, int sync, int *status, int *max_iters, int nb_recon,
-                                                      IfaceDev Ih, LevelGeo gh, const S *__restrict__ fh, int slot)
+__global__ void __launch_bounds__(128) k_recon_hist(const __grid_constant__ IfaceDev Ir, const __grid_constant__ LevelDev F,
+                                                      const __grid_constant__ LevelDev Cl, const S *__restrict__ ff,
+                                                      const __grid_constant__ TimeW tw, int sync, int *status, int *max_iters,
+                                                      int nb_recon, const __grid_constant__ IfaceDev Ih,
+                                                      const __grid_constant__ LevelGeo gh, const S *__restrict__ fh, int slot)
 {
     pdl_enter();
     if ((int)blockIdx.x < nb_recon) {
@@ -1015,14 +1017,16 @@ __global__ void __launch_bounds__(128) k_recon_hist(IfaceDev Ir, LevelDev F, Lev
 }
 
 template <int Q, typename S>
-__global__ void __launch_bounds__(128) k_hist(IfaceDev I, LevelGeo gc, const S *__restrict__ fc, int slot, int seed)
+__global__ void __launch_bounds__(128) k_hist(const __grid_constant__ IfaceDev I, const __grid_constant__ LevelGeo gc,
+                                             const S *__restrict__ fc, int slot, int seed)
 {
     hist_node<Q, S>(blockIdx.x, I, gc, fc, slot, seed);
 }
 
 template <int Q, typename S, bool NODE>
-__global__ void __launch_bounds__(128) k_grad_ie(IfaceDev I, LevelDev F, LevelDev Cl, const S *__restrict__ ff,
-                                                   TimeW tw, int sync, int nb_grad)
+__global__ void __launch_bounds__(128) k_grad_ie(const __grid_constant__ IfaceDev I, const __grid_constant__ LevelDev F,
+                                                   const __grid_constant__ LevelDev Cl, const S *__restrict__ ff,
+                                                   const __grid_constant__ TimeW tw, int sync, int nb_grad)
 {
     pdl_enter();
     if ((int)blockIdx.x < nb_grad) {
@@ -1031,6 +1035,40 @@ __global__ void __launch_bounds__(128) k_grad_ie(IfaceDev I, LevelDev F, LevelDe
     } else {
         if constexpr (NODE) ie_node<Q, S>(blockIdx.x - nb_grad, I, F, ff);
         else ie_seg<Q, S>(blockIdx.x - nb_grad, I, F, ff);
+    }
+}
+
+// S and C of the hanging nodes of a level (D3Q19): the same 4-point stencils over the
+// level's TF rows as their missing populations (tensor order over the node's odd axes,
+// up to 16 points), written to the hanging nodes' own table rows, so that the bulk
+// collision reads them like a TF node's.  One hanging node per thread; launched after
+// the gradient launch that writes the TF rows.  The sum runs in stencil order, as the
+// 2-D tile kernel's in-place interpolation does.
+template <typename R>
+__global__ void __launch_bounds__(128) k_ie_sc(const __grid_constant__ LevelDev F)
+{
+    pdl_enter();
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= F.n_ie) return;
+    R *tS = (R *)F.if_S, *tC = (R *)F.if_C;
+    const int nst = F.ie_nst[e];
+    R Sv[6], Cv[6];
+#pragma unroll
+    for (int q = 0; q < 6; q++) Sv[q] = Cv[q] = R(0);
+    for (int j = 0; j < nst; j++) {
+        const int tf = F.ie_st[e * 16 + j];
+        const R wj = ((const R *)F.ie_w)[e * 16 + j];
+#pragma unroll
+        for (int q = 0; q < 6; q++) {
+            Sv[q] += wj * tS[(long long)q * F.nif + tf];
+            Cv[q] += wj * tC[(long long)q * F.nif + tf];
+        }
+    }
+    const long long row = F.ie_base + e;
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+        tS[(long long)q * F.nif + row] = Sv[q];
+        tC[(long long)q * F.nif + row] = Cv[q];
     }
 }
 
@@ -1312,7 +1350,7 @@ __device__ __forceinline__ bool bulk2d_tile(const LevelDev &Lv, const S *__restr
 }
 
 template <int Q, typename S, int TX, int TYT, int NR>
-__global__ void __launch_bounds__(TX *TYT, sizeof(S) == 8 ? 1 : (TX * TYT >= 256 ? 1024 / (TX * TYT) : 4)) k_bulk2d(LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
+__global__ void __launch_bounds__(TX *TYT, sizeof(S) == 8 ? 1 : (TX * TYT >= 256 ? 1024 / (TX * TYT) : 4)) k_bulk2d(const __grid_constant__ LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
                                                      typename St<S>::R tau, typename St<S>::R om,
                                                      typename St<S>::R sigma, typename St<S>::R spsi)
 {
