@@ -606,6 +606,9 @@ int build_interfaces(lbm_h h)
                         I.ie_w[(size_t)e * 16 + m] = wt[0][i0] * wt[1][i1] * wt[2][i2];
                         m++;
                     }
+            // the kernels read a fixed number of stencil slots: 4 in 2-D, 16 in 3-D
+            if (m > (h->D == 2 ? 4 : 16))
+                return fail(nullptr, LBM_ERR_BAD_DESC, "internal: a hanging-node stencil of %d points", m);
             I.ie_nst[e] = m;
         }
         F.nTFP = nTF;

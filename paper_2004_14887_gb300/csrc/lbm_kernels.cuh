@@ -516,6 +516,11 @@ __device__ __forceinline__ void grad_seg(int bid, IfaceDev I, LevelDev F, LevelD
 // next to corners) of missing populations; macros are the moments.  One W-lane
 // segment per hanging node, lane i completes population i.  S and C of hanging
 // nodes are interpolated with the same stencil where they are used (collide_store).
+// stencil slots a hanging node may use (rows of [n_ie][16]): 4 points along its odd
+// axis in 2-D, a 4 x 4 tensor over its two odd in-face axes in 3-D
+template <int D>
+constexpr int kIeSlots = D == 2 ? 4 : 16;
+
 template <int Q, typename S>
 __device__ __forceinline__ void ie_seg(int bid, IfaceDev I, LevelDev F, const S *__restrict__ ff)
 {
@@ -540,8 +545,19 @@ __device__ __forceinline__ void ie_seg(int bid, IfaceDev I, LevelDev F, const S 
             const int s = nb_index(F.g, I.ie_f[3 * e], I.ie_f[3 * e + 1], I.ie_f[3 * e + 2], -c[0], -c[1], -c[2]);
             if (s >= 0) v = St<S>::ld(ff, (long long)i * F.g.pitch + s, lane_shift<Q>(F.g, i));
         } else {
+            // every stencil slot read at once, then the used TF rows at once
+            constexpr int NS = kIeSlots<D>;
             const R *iw = (const R *)I.ie_w;
-            for (int k = 0; k < nst; k++) v += iw[e * 16 + k] * fpop[(long long)i * nif + I.ie_st[e * 16 + k]];
+            int st[NS];
+            R w[NS];
+#pragma unroll
+            for (int k = 0; k < NS; k++) {
+                st[k] = I.ie_st[e * 16 + k];
+                w[k] = iw[e * 16 + k];
+            }
+#pragma unroll
+            for (int k = 0; k < NS; k++)
+                if (k < nst) v += w[k] * fpop[(long long)i * nif + st[k]];
         }
         fpop[(long long)i * nif + row] = v;
     }
@@ -959,6 +975,17 @@ __device__ __forceinline__ void ie_node(int bid, IfaceDev I, LevelDev F, const S
     const unsigned kfm = I.ie_kf[e];
     const int nst = I.ie_nst[e];
     const int x = I.ie_f[3 * e], y = I.ie_f[3 * e + 1], z = I.ie_f[3 * e + 2];
+    // the stencil slots in registers once: the gathers of every missing population are
+    // then independent loads (the table stores between populations would otherwise
+    // force the slots to be read again after each)
+    constexpr int NS = kIeSlots<D>;
+    int st[NS];
+    R w[NS];
+#pragma unroll
+    for (int k = 0; k < NS; k++) {
+        st[k] = I.ie_st[e * 16 + k];
+        w[k] = iw[e * 16 + k];
+    }
     R rho = R(0), m[3] = {R(0), R(0), R(0)};
     static_for<Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
@@ -967,7 +994,9 @@ __device__ __forceinline__ void ie_node(int bid, IfaceDev I, LevelDev F, const S
             const int s = nb_index(F.g, x, y, z, -L::c(i, 0), -L::c(i, 1), -L::c(i, 2));
             if (s >= 0) v = St<S>::ld(ff, (long long)i * F.g.pitch + s, F.g.shift[i]);
         } else {
-            for (int k = 0; k < nst; k++) v += iw[e * 16 + k] * fpop[(long long)i * nif + I.ie_st[e * 16 + k]];
+#pragma unroll
+            for (int k = 0; k < NS; k++)
+                if (k < nst) v += w[k] * fpop[(long long)i * nif + st[k]];
         }
         fpop[(long long)i * nif + row] = v;
         rho += v;
@@ -1052,16 +1081,24 @@ __global__ void __launch_bounds__(128) k_ie_sc(const __grid_constant__ LevelDev 
     if (e >= F.n_ie) return;
     R *tS = (R *)F.if_S, *tC = (R *)F.if_C;
     const int nst = F.ie_nst[e];
+    int st[16];
+    R w[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+        st[j] = F.ie_st[e * 16 + j];
+        w[j] = ((const R *)F.ie_w)[e * 16 + j];
+    }
     R Sv[6], Cv[6];
 #pragma unroll
     for (int q = 0; q < 6; q++) Sv[q] = Cv[q] = R(0);
-    for (int j = 0; j < nst; j++) {
-        const int tf = F.ie_st[e * 16 + j];
-        const R wj = ((const R *)F.ie_w)[e * 16 + j];
 #pragma unroll
-        for (int q = 0; q < 6; q++) {
-            Sv[q] += wj * tS[(long long)q * F.nif + tf];
-            Cv[q] += wj * tC[(long long)q * F.nif + tf];
+    for (int j = 0; j < 16; j++) {
+        if (j < nst) {
+#pragma unroll
+            for (int q = 0; q < 6; q++) {
+                Sv[q] += w[j] * tS[(long long)q * F.nif + st[j]];
+                Cv[q] += w[j] * tC[(long long)q * F.nif + st[j]];
+            }
         }
     }
     const long long row = F.ie_base + e;
@@ -1150,21 +1187,32 @@ __device__ __forceinline__ void collide_store(const LevelDev &Lv, typename St<S>
             }
         fd_gradients<D, R>(nr, nu, R(0.5), Sv, Cv);
     } else if (tag >= Lv.ie_base && tag < Lv.ie_base + Lv.n_ie) {
-        // hanging node: S and C by the same 4-point stencil as its missing populations
+        // hanging node: S and C by the same stencil as its missing populations (D2Q9:
+        // 4 or 2 points along the interface).  The stencil rows are [n_ie][16], so the
+        // four slots are read at once with the count, then the table rows of the used
+        // slots at once: two dependent round trips instead of two per point
+        static_assert(L::D == 2, "2-D stencils have at most 4 points");
         const R *tS = (const R *)Lv.if_S, *tC = (const R *)Lv.if_C;
         const int e = tag - Lv.ie_base, nst = Lv.ie_nst[e];
+        int tf[4];
+        R wj[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            tf[j] = Lv.ie_st[e * 16 + j];
+            wj[j] = ((const R *)Lv.ie_w)[e * 16 + j];
+        }
 #pragma unroll
         for (int k = 0; k < 6; k++) {
             Sv[k] = R(0);
             Cv[k] = R(0);
         }
-        for (int j = 0; j < nst; j++) {
-            const int tf = Lv.ie_st[e * 16 + j];
-            const R wj = ((const R *)Lv.ie_w)[e * 16 + j];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (j >= nst) break;
 #pragma unroll
             for (int k = 0; k < 6; k++) {
-                Sv[k] += wj * tS[(long long)k * Lv.nif + tf];
-                Cv[k] += wj * tC[(long long)k * Lv.nif + tf];
+                Sv[k] += wj[j] * tS[(long long)k * Lv.nif + tf[j]];
+                Cv[k] += wj[j] * tC[(long long)k * Lv.nif + tf[j]];
             }
         }
     } else {
