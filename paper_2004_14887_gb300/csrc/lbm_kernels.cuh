@@ -811,12 +811,17 @@ __device__ __forceinline__ void recon_node(int bid, IfaceDev I, LevelDev F, Leve
     const Feq64 nd = feq64_node<D>((double)X[0], Xd);
     static_for<Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
-        // FP64 equilibrium / non-equilibrium rescaling
-        const double fe = feq64_pop<Q, i>(nd);
+        // FP64 equilibrium / non-equilibrium rescaling; the equilibrium only where a
+        // rescaling uses it (gamma_i = c, or every population of a sync sub-step)
+        const bool gc_i = (gcm >> i) & 1u;
         const double fh = (double)fhat[i];
-        const double v = ((gcm >> i) & 1u) ? fe + I.R * (fh - fe) : fh;
+        double v = fh;
+        if (gc_i || sync) {
+            const double fe = feq64_pop<Q, i>(nd);
+            if (gc_i) v = fe + I.R * (fh - fe);
+            if (sync) cpop[(long long)i * Cl.nif + I.tfc_base + t] = (R)(fe + (v - fe) * I.Rinv);
+        }
         fpop[(long long)i * F.nif + t] = (R)v;
-        if (sync) cpop[(long long)i * Cl.nif + I.tfc_base + t] = (R)(fe + (v - fe) * I.Rinv);
     });
     R *fmac = (R *)F.if_mac;
 #pragma unroll
@@ -1320,36 +1325,49 @@ __device__ __forceinline__ bool bulk2d_tile(const LevelDev &Lv, const S *__restr
         }
     } else {
         // own positions (wrapped when a ragged tile sits past a periodic seam) and the
-        // halo position: tags first, then every pull
+        // halo position: their tags, and with them every bulk pull of a position inside
+        // the box (a bulk node's sources are nodes, reached with a one-step wrap on
+        // periodic axes; for any other position inside the box the same one-step wrap
+        // keeps the address inside the box, and its value is replaced below), so that a
+        // bulk node of a general tile waits for one round trip, not two
         int ox[NR], oy[NR];
+        bool okp[NR];
 #pragma unroll
         for (int r = 0; r < NR; r++) {
             ox[r] = x;
             oy[r] = Y0 + tr + r * TYT;
-            const bool ok = wrap_coord(ox[r], g.n[0], g.per[0]) && wrap_coord(oy[r], g.n[1], g.per[1]);
-            otag[r] = ok ? Lv.tag[ox[r] + g.px * oy[r]] : TAG_HOLE;
+            okp[r] = wrap_coord(ox[r], g.n[0], g.per[0]) && wrap_coord(oy[r], g.n[1], g.per[1]);
+            otag[r] = okp[r] ? Lv.tag[ox[r] + g.px * oy[r]] : TAG_HOLE;
         }
         int qx = X0 + hx - 1, qy = Y0 + hy - 1;
         const bool hvalid = hb >= 0 && wrap_coord(qx, g.n[0], g.per[0]) && wrap_coord(qy, g.n[1], g.per[1]);
         htag = hvalid ? Lv.tag[qx + g.px * qy] : TAG_HOLE;
-        const R *pop = (const R *)Lv.if_pop;
 #pragma unroll
         for (int i = 0; i < Q; i++) {
             const S *pi = fsrc + (long long)i * g.pitch;
 #pragma unroll
             for (int r = 0; r < NR; r++) {
-                // bulk sources are nodes: a one-step wrap on periodic axes is all they need
                 int sx = ox[r] - L::c(i, 0), sy = oy[r] - L::c(i, 1);
                 sx += (sx < 0) ? g.n[0] : ((sx >= g.n[0]) ? -g.n[0] : 0);
                 sy += (sy < 0) ? g.n[1] : ((sy >= g.n[1]) ? -g.n[1] : 0);
-                f[r][i] = otag[r] == TAG_BULK ? St<S>::ld(pi, sx + g.px * sy, g.shift[i])
-                                              : (otag[r] >= 0 ? pop[(long long)i * Lv.nif + otag[r]] : R(0));
+                f[r][i] = okp[r] ? St<S>::ld(pi, sx + g.px * sy, g.shift[i]) : R(0);
             }
             int hsx = qx - L::c(i, 0), hsy = qy - L::c(i, 1);
             hsx += (hsx < 0) ? g.n[0] : ((hsx >= g.n[0]) ? -g.n[0] : 0);
             hsy += (hsy < 0) ? g.n[1] : ((hsy >= g.n[1]) ? -g.n[1] : 0);
-            fh[i] = htag == TAG_BULK ? St<S>::ld(pi, hsx + g.px * hsy, g.shift[i])
-                                     : (htag >= 0 ? pop[(long long)i * Lv.nif + htag] : R(0));
+            fh[i] = hvalid ? St<S>::ld(pi, hsx + g.px * hsy, g.shift[i]) : R(0);
+        }
+        // positions that are not bulk nodes: table rows (interface) or nothing (hole)
+        const R *pop = (const R *)Lv.if_pop;
+#pragma unroll
+        for (int r = 0; r < NR; r++)
+            if (otag[r] != TAG_BULK) {
+#pragma unroll
+                for (int i = 0; i < Q; i++) f[r][i] = otag[r] >= 0 ? pop[(long long)i * Lv.nif + otag[r]] : R(0);
+            }
+        if (htag != TAG_BULK) {
+#pragma unroll
+            for (int i = 0; i < Q; i++) fh[i] = htag >= 0 ? pop[(long long)i * Lv.nif + htag] : R(0);
         }
     }
     // macros of every own position (a position past a periodic seam stands for the
