@@ -515,7 +515,9 @@ __device__ __forceinline__ void grad_seg(int bid, IfaceDev I, LevelDev F, LevelD
 // 4-point 1-D Lagrange along the interface (tensor order over odd axes, one-sided
 // next to corners) of missing populations; macros are the moments.  One W-lane
 // segment per hanging node, lane i completes population i.  S and C of hanging
-// nodes are interpolated with the same stencil where they are used (collide_store).
+// nodes are interpolated with the same stencil by the 2-D tile kernel where they are
+// used (collide_store) and for D3Q19 by k_ie_sc after this launch.
+
 // stencil slots a hanging node may use (rows of [n_ie][16]): 4 points along its odd
 // axis in 2-D, a 4 x 4 tensor over its two odd in-face axes in 3-D
 template <int D>
@@ -963,8 +965,9 @@ __device__ __forceinline__ void grad_node(int bid, IfaceDev I, LevelDev F, Level
 // ------------------------------------------------------------------ hanging nodes
 // 4-point 1-D Lagrange along the interface (tensor order over odd axes, one-sided
 // next to corners) of missing populations; macros are the moments.  One hanging node
-// per thread.  S and C of hanging nodes are interpolated with the same stencil where
-// they are used (collide_store).
+// per thread.  S and C of hanging nodes are interpolated with the same stencil by the
+// 2-D tile kernel where they are used (collide_store) and for D3Q19 by k_ie_sc after
+// this launch.
 template <int Q, typename S>
 __device__ __forceinline__ void ie_node(int bid, IfaceDev I, LevelDev F, const S *__restrict__ ff)
 {
