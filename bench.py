@@ -173,13 +173,13 @@ def _workloads():
 
 
 def kernel_source_key(csrc):
-    """Hash of the device code (kernel and device headers) with comments and blank
-    lines removed: a traffic figure measured by ncu stays valid while the code is
-    unchanged."""
+    """Hash of the library sources (kernels, device headers and the host code that
+    chooses launch shapes) with comments and blank lines removed: a traffic figure
+    measured by ncu stays valid while the code is unchanged."""
     import hashlib
 
     h = hashlib.sha1()
-    for name in ("lbm_kernels.cuh", "lbm_device.cuh"):
+    for name in sorted(f for f in os.listdir(csrc) if f.endswith((".cuh", ".cu"))):
         txt = open(os.path.join(csrc, name)).read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
         txt = re.sub(r"//[^\n]*", "", txt)

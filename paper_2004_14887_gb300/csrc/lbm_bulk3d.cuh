@@ -201,8 +201,9 @@ __device__ __forceinline__ void pair_moments19(const R (&v)[19], R (&m)[10])
 // with V_b^a = T_ab + W_b, where W_b = -(1/3) sum_{a!=b} T_ab is the whole sum of the
 // axis population along +b.  Pq is sum c c f of the pre-collision populations with
 // cs2 sum f taken off its diagonal.  With SHIFT the values returned are f_i - s_i with
-// s_i = w_i (she_i + sho_i), s_opp(i) = w_i (she_i - sho_i).
-template <typename R, bool SHIFT, typename Put>
+// s_i = w_i (she_i + sho_i), s_opp(i) = w_i (she_i - sho_i); PLAIN: the shift of a
+// fluid at rest, s_i = w_i (she_i = 1, sho_i = 0), folded into the constants.
+template <typename R, bool SHIFT, bool PLAIN, typename Put>
 __device__ __forceinline__ void hrr_pairs19(R rho, const R *u, const R *Pq, const R *S, const R *C, R tau, R om,
                                             R sigma, R spsi, const float *she, const float *sho, Put &&put)
 {
@@ -240,7 +241,9 @@ __device__ __forceinline__ void hrr_pairs19(R rho, const R *u, const R *Pq, cons
         constexpr int i = decltype(ic)::value;
         R e = rho + R(4.5) * h2;
         R o = r3 * cu + R(13.5) * h3;
-        if constexpr (SHIFT) {
+        if constexpr (SHIFT && PLAIN) {
+            e -= R(1);
+        } else if constexpr (SHIFT) {
             e -= R(she[i]);
             o -= R(sho[i]);
         }
@@ -250,7 +253,7 @@ __device__ __forceinline__ void hrr_pairs19(R rho, const R *u, const R *Pq, cons
     };
     {
         const R e = rho - R(4.5) * ctr;  // rest population: E = rho - 9/2 cs2 tr B, O = 0
-        if constexpr (SHIFT) put(std::integral_constant<int, 0>{}, R(L::w(0)) * (e - R(she[0])));
+        if constexpr (SHIFT) put(std::integral_constant<int, 0>{}, R(L::w(0)) * (e - (PLAIN ? R(1) : R(she[0]))));
         else put(std::integral_constant<int, 0>{}, R(L::w(0)) * e);
     }
     out(std::integral_constant<int, 1>{}, u[0], B[0] - ctr, W[0]);
@@ -282,8 +285,10 @@ __device__ __forceinline__ void hrr_pairs19(R rho, const R *u, const R *Pq, cons
 // are bounded: on time-out the kernel sets ST_TIMEOUT, waits (bounded) for its copies
 // in flight and returns.  withhold_block / withhold_k (test hook, -1: none): the block
 // with that linear index does not issue the copies of its k-th stage, so its wait for
-// them runs out.
-template <int Q, typename S, int TX, int TY>
+// them runs out.  PLAIN (FP16 storage with u_shift = 0): the shift's moments and pair
+// constants are compile-time values; the results are the same bits as with the
+// general shift tables, whose entries are then exactly 1, 0 and 1/3 in FP32.
+template <int Q, typename S, int TX, int TY, bool PLAIN = false>
 __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
     k_bulk3d(const __grid_constant__ TMaps tmaps, const __grid_constant__ LevelDev Lv, const S *__restrict__ fsrc, S *__restrict__ fdst,
              typename St<S>::R tau, typename St<S>::R om, typename St<S>::R sigma, typename St<S>::R spsi, int zc,
@@ -489,7 +494,15 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
             v[i] = raw<S>(st[i * BOX + b - L::c(i, 1) * BW - L::c(i, 0)]);
         });
         pair_moments19<R, decltype(only_j)::value>(v, m);
-        if constexpr (SHIFT) {
+        if constexpr (SHIFT && PLAIN) {
+            // the moments of s_i = w_i: 1, 0, c_s^2 I
+            m[0] += R(1);
+            if constexpr (!decltype(only_j)::value) {
+                m[4] += R(1.0 / 3.0);
+                m[5] += R(1.0 / 3.0);
+                m[6] += R(1.0 / 3.0);
+            }
+        } else if constexpr (SHIFT) {
             constexpr int nm = decltype(only_j)::value ? 4 : 10;
 #pragma unroll
             for (int q = 0; q < nm; q++) m[q] += R(Lv.smom[q]);
@@ -647,7 +660,7 @@ __global__ void __launch_bounds__(TX *TY, sizeof(S) == 8 ? 1 : 2)
                 }
             }
             S *dst = fdst + (x + g.px * y + (long long)n01 * z);
-            hrr_pairs19<R, SHIFT>(rho_c, z0, pq_c, Sv, Cv, tau, om, sigma, spsi, Lv.she, Lv.sho,
+            hrr_pairs19<R, SHIFT, PLAIN>(rho_c, z0, pq_c, Sv, Cv, tau, om, sigma, spsi, Lv.she, Lv.sho,
                                   [&](auto ic, R v) {
                                       constexpr int i = decltype(ic)::value;
                                       if constexpr (SHIFT) dst[(long long)i * pitch] = __float2half_rn(v);

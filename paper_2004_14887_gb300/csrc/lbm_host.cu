@@ -115,6 +115,7 @@ struct lbm_hierarchy {
     int withhold_level = -1, withhold_block = -1, withhold_k = -1;
     unsigned long long withhold_limit_ns = 0;
     float shift[19] = {};          // FP16-shifted storage: f_i - shift[i] (f_i^eq(1, u_shift))
+    bool plain_shift = false;      // FP16 storage with u_shift = 0 (shift[i] = w_i)
     double *d_partial = nullptr, *d_red = nullptr;
     int red_blocks = 0;
     long long ncoarse = 0;  // coarse steps done since init
@@ -888,9 +889,14 @@ template <typename S>
 int bulk3d_prepare(int *per_sm)
 {
     using G = Stage3<19, S, T3X, T3Y>;
-    auto kern = k_bulk3d<19, S, T3X, T3Y>;
+    auto kern = k_bulk3d<19, S, T3X, T3Y, false>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem_bytes) != cudaSuccess)
         return -1;
+    if constexpr (std::is_same<S, __half>::value) {
+        if (cudaFuncSetAttribute(k_bulk3d<19, S, T3X, T3Y, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)G::smem_bytes) != cudaSuccess)
+            return -1;
+    }
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, T3X * T3Y, G::smem_bytes) != cudaSuccess) return -1;
     return 0;
 }
@@ -1172,11 +1178,15 @@ struct Sched {
         const R tau = (R)v.tau, om = (R)(1.0 - 1.0 / v.tau), sig = (R)h->d.sigma, sps = (R)spsi;
         if constexpr (Lat<Q>::D == 2)
             launch_bulk2d<Q, S>(h, l, v.tile_cfg, src, dst, tau, om, sig, sps, st);
-        else
-            launch_chained(k_bulk3d<Q, S, T3X, T3Y>, nt, dim3(T3X * T3Y), Stage3<Q, S, T3X, T3Y>::smem_bytes, st,
+        else {
+            auto k3 = k_bulk3d<Q, S, T3X, T3Y, false>;
+            if constexpr (std::is_same<S, __half>::value)
+                if (h->plain_shift) k3 = k_bulk3d<Q, S, T3X, T3Y, true>;
+            launch_chained(k3, nt, dim3(T3X * T3Y), Stage3<Q, S, T3X, T3Y>::smem_bytes, st,
                            v.tmap[src == v.f[0] ? 0 : 1], level_dev(h, l), (const S *)src, (S *)dst, tau, om, sig,
                            sps, v.zc, h->d_status, h->withhold_level == l ? h->withhold_limit_ns : kWaitLimitNs,
                            h->withhold_level == l ? h->withhold_block : -1, h->withhold_level == l ? h->withhold_k : -1);
+        }
         h->launch_counter++;
         if (h->timing) {
             cudaEventRecord(h->ev_pool[ev + 1], h->stream);
@@ -1415,6 +1425,8 @@ static int create_impl(const lbm_hierarchy_desc *desc, const uint8_t *const *mas
     h->nl = desc->n_levels;
     for (int i = 0; i < h->Q; i++)  // s_i = f_i^eq(1, u_shift): w_i for u_shift = 0
         h->shift[i] = (float)(h->Q == 9 ? feq_one<9>(i, 1.0, desc->u_shift) : feq_one<19>(i, 1.0, desc->u_shift));
+    h->plain_shift = desc->storage == LBM_F16S && desc->u_shift[0] == 0.0 && desc->u_shift[1] == 0.0 &&
+                     desc->u_shift[2] == 0.0;
     for (int l = 1; l < h->nl && masks; l++) {
         if (!masks[l]) continue;
         size_t cells = 1;
